@@ -1,0 +1,361 @@
+/*
+ * CPU oracle for the short-range particle-particle force path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header or constant with the CUDA path.
+ *
+ * Everything here is the plain definition, written to be checked by eye:
+ *
+ *   a_i = sum_{j != i, s_ij < r_c^2} m_j f_SR(s_ij) d_ij,
+ *   f_SR(s) = (s + eps)^(-3/2) - poly(s),  poly(s) = sum_k c_k s^k,
+ *
+ * (Eq. 4 of the paper, the short-range kernel; s = r.r; the cutoff test is
+ * folded into the pair loop as in the paper's discussion of the select
+ * instruction, Sec. IV-B), with d_ij = x_j - x_i taken as the minimum periodic
+ * image, evaluated in float64 by brute force over all j.  Positions and masses
+ * are float64 arrays (float32 inputs widened, or a float64 trajectory).
+ *
+ * The chaining-mesh binning reference follows the float32 expression sequence
+ * that defines a particle's cell (the build's reading of the paper's spatial
+ * partition, Sec. IV-A: a mesh replaces the RCB tree): wrap into [0, L), cell
+ * index per axis, cell-relative offset.  Each step is a single IEEE float32
+ * operation with round-to-nearest; this file must be compiled with
+ * -ffp-contract=off so that no step is fused.
+ *
+ * Compile: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int ora_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Chaining mesh geometry                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* n = floor(L / cell_min) cells per side (float64 quotient); w = L / n and
+ * inv_w = n / L, each one float32 division. */
+void ora_mesh(float L, float cell_min, int32_t *n_out, float *w_out, float *inv_w_out)
+{
+    int32_t n = (int32_t)floor((double)L / (double)cell_min);
+    float nf = (float)n;
+    *n_out = n;
+    *w_out = L / nf;
+    *inv_w_out = nf / L;
+}
+
+/* Wrap one float32 coordinate into [0, L): q = floor(x / L); x - q L; then one
+ * correction step for the two rounding edge cases. */
+static float wrap32(float x, float L)
+{
+    float q = floorf(x / L);
+    float ql = q * L;
+    float xw = x - ql;
+    if (xw < 0.0f) xw = xw + L;
+    if (xw >= L) xw = xw - L;
+    return xw;
+}
+
+static int32_t cell1(float xw, float inv_w, int32_t n)
+{
+    float t = xw * inv_w;
+    int32_t c = (int32_t)floorf(t);
+    if (c > n - 1) c = n - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+/* Binning of one volume.  Outputs: cell_of[i] (cell of particle i), counts per
+ * cell, and the stable order: perm[k] = original index of the particle in
+ * sorted slot k, particles ordered by cell and, within a cell, by original
+ * index.  sorted4[4k..4k+3] = (ox, oy, oz, m) with o = xw - c w (float32).
+ * cell_start has n^3 + 1 entries.  Returns 0. */
+int ora_bin(const float *x, const float *y, const float *z, const float *m, int64_t N,
+            float L, int32_t n, float w, float inv_w,
+            int32_t *cell_of, int32_t *cell_start, int32_t *perm, float *sorted4)
+{
+    int64_t nc = (int64_t)n * n * n;
+    int64_t *cnt = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t cx = cell1(wrap32(x[i], L), inv_w, n);
+        int32_t cy = cell1(wrap32(y[i], L), inv_w, n);
+        int32_t cz = cell1(wrap32(z[i], L), inv_w, n);
+        int32_t c = (cz * n + cy) * n + cx;
+        cell_of[i] = c;
+        cnt[c] += 1;
+    }
+    int64_t run = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        cell_start[c] = (int32_t)run;
+        run += cnt[c];
+        cnt[c] = cell_start[c]; /* becomes the fill cursor */
+    }
+    cell_start[nc] = (int32_t)run;
+    /* visiting particles in index order makes the placement stable */
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t c = cell_of[i];
+        int64_t k = cnt[c]++;
+        perm[k] = (int32_t)i;
+        float xw = wrap32(x[i], L), yw = wrap32(y[i], L), zw = wrap32(z[i], L);
+        int32_t cx = c % n, cy = (c / n) % n, cz = c / (n * n);
+        float ox = xw - (float)cx * w;
+        float oy = yw - (float)cy * w;
+        float oz = zw - (float)cz * w;
+        sorted4[4 * k + 0] = ox;
+        sorted4[4 * k + 1] = oy;
+        sorted4[4 * k + 2] = oz;
+        sorted4[4 * k + 3] = m[i];
+    }
+    free(cnt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cell-pair interaction lists                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Stencil reach: offsets with |delta_a| <= R, R = ceil(r_c / w). */
+int32_t ora_reach(float w, float rcut)
+{
+    return (int32_t)ceil((double)rcut / (double)w);
+}
+
+/* Two cells whose integer offsets are delta can hold a pair closer than r_c
+ * iff the minimum distance between the boxes is below r_c:
+ * sum_a max(0, |delta_a| - 1)^2 w^2 < r_c^2, in float64. */
+static int cells_within(int dx, int dy, int dz, double w, double rc)
+{
+    double gx = abs(dx) > 1 ? (double)(abs(dx) - 1) : 0.0;
+    double gy = abs(dy) > 1 ? (double)(abs(dy) - 1) : 0.0;
+    double gz = abs(dz) > 1 ? (double)(abs(dz) - 1) : 0.0;
+    return (gx * gx + gy * gy + gz * gz) * w * w < rc * rc;
+}
+
+/* Per-cell neighbour lists of one volume, canonical order: for cell c
+ * (ascending), offsets (dz, dy, dx) ascending lexicographically over
+ * [-R, R]^3 restricted to cells_within.  Each entry: neighbour cell id and a
+ * periodic shift code (sz+1)*9 + (sy+1)*3 + (sx+1), s_a in {-1, 0, 1} the
+ * image of the neighbour along axis a.  nbr_off has n^3 + 1 entries.  When
+ * nbr_cell is NULL only the counts are produced.  Returns the entry count,
+ * or -1 if the mesh is too coarse for a unique image (n < 2R + 1). */
+int64_t ora_lists(int32_t n, float w, float rcut, int64_t *nbr_off, int32_t *nbr_cell,
+                  int8_t *nbr_shift)
+{
+    int32_t R = ora_reach(w, rcut);
+    if (n < 2 * R + 1) return -1;
+    int64_t nc = (int64_t)n * n * n;
+    int64_t e = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int32_t cx = (int32_t)(c % n), cy = (int32_t)((c / n) % n), cz = (int32_t)(c / ((int64_t)n * n));
+        if (nbr_off) nbr_off[c] = e;
+        for (int dz = -R; dz <= R; ++dz)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                    if (!cells_within(dx, dy, dz, (double)w, (double)rcut)) continue;
+                    int32_t px = cx + dx, py = cy + dy, pz = cz + dz;
+                    int sx = 0, sy = 0, sz = 0;
+                    if (px < 0) { px += n; sx = -1; } else if (px >= n) { px -= n; sx = 1; }
+                    if (py < 0) { py += n; sy = -1; } else if (py >= n) { py -= n; sy = 1; }
+                    if (pz < 0) { pz += n; sz = -1; } else if (pz >= n) { pz -= n; sz = 1; }
+                    if (nbr_cell) {
+                        nbr_cell[e] = (pz * n + py) * n + px;
+                        nbr_shift[e] = (int8_t)((sz + 1) * 9 + (sy + 1) * 3 + (sx + 1));
+                    }
+                    ++e;
+                }
+    }
+    if (nbr_off) nbr_off[nc] = e;
+    return e;
+}
+
+/* Work items: each cell's particle range cut into consecutive chunks of at
+ * most T particles, cells ascending.  Each task: (cell, begin, end) in sorted
+ * slots.  Returns the task count (tasks may be NULL to count). */
+int64_t ora_tasks(const int32_t *cell_start, int64_t ncells, int32_t T, int32_t *tasks3)
+{
+    int64_t t = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        int32_t b = cell_start[c], e = cell_start[c + 1];
+        for (int32_t i = b; i < e; i += T) {
+            if (tasks3) {
+                tasks3[3 * t + 0] = (int32_t)c;
+                tasks3[3 * t + 1] = i;
+                tasks3[3 * t + 2] = (i + T < e) ? i + T : e;
+            }
+            ++t;
+        }
+    }
+    return t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Short-range force (Eq. 4), brute force in float64                         */
+/* ------------------------------------------------------------------------ */
+
+static double min_image(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+static double poly5(const double *c, double s)
+{
+    return c[0] + s * (c[1] + s * (c[2] + s * (c[3] + s * (c[4] + s * c[5]))));
+}
+
+static double dpoly5(const double *c, double s)
+{
+    return c[1] + s * (2.0 * c[2] + s * (3.0 * c[3] + s * (4.0 * c[4] + s * 5.0 * c[5])));
+}
+
+/* f_SR(s) = (s + eps)^-3/2 - poly(s) */
+double ora_fsr(double s, double eps, const double *c)
+{
+    return pow(s + eps, -1.5) - poly5(c, s);
+}
+
+/* f_SR'(s) = -3/2 (s + eps)^-5/2 - poly'(s) */
+double ora_dfsr(double s, double eps, const double *c)
+{
+    return -1.5 * pow(s + eps, -2.5) - dpoly5(c, s);
+}
+
+/* Accelerations of the S target particles targets[0..S-1] from all N
+ * particles of one periodic box of side L. */
+void ora_sr_force(const double *x, const double *y, const double *z, const double *m, int64_t N,
+                  double L, double eps, double rcut, const double *c,
+                  const int64_t *targets, int64_t S, double *ax, double *ay, double *az)
+{
+    double rc2 = rcut * rcut;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < S; ++t) {
+        int64_t i = targets[t];
+        double xi = x[i], yi = y[i], zi = z[i];
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[j] - xi, L);
+            double dy = min_image(y[j] - yi, L);
+            double dz = min_image(z[j] - zi, L);
+            double s = dx * dx + dy * dy + dz * dz;
+            if (!(s < rc2)) continue;
+            double g = m[j] * ora_fsr(s, eps, c);
+            sx += g * dx;
+            sy += g * dy;
+            sz += g * dz;
+        }
+        ax[t] = sx;
+        ay[t] = sy;
+        az[t] = sz;
+    }
+}
+
+/* Number of ordered pairs (i, j), j != i, with s_ij < r_c^2. */
+int64_t ora_pair_count(const double *x, const double *y, const double *z, int64_t N,
+                       double L, double rcut, const int64_t *targets, int64_t S)
+{
+    double rc2 = rcut * rcut;
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t t = 0; t < S; ++t) {
+        int64_t i = targets[t];
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[j] - x[i], L);
+            double dy = min_image(y[j] - y[i], L);
+            double dz = min_image(z[j] - z[i], L);
+            if (dx * dx + dy * dy + dz * dz < rc2) total += 1;
+        }
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the force (vector-Jacobian product), float64                   */
+/* ------------------------------------------------------------------------ */
+
+/* Given the cotangent lam_k = dL/da_k of every particle's acceleration,
+ * returns for each target i:
+ *   dL/dx_i = sum_j [ m_i J(d_ij) lam_j - m_j J(d_ij) lam_i ],
+ *   J(d) = f(s) I + 2 f'(s) d d^T   (the Jacobian of f(d.d) d),
+ * because x_i enters a_i through every d_ij = x_j - x_i (sign -) and every a_j
+ * through d_ji = x_i - x_j (sign +, J even in d).  And
+ *   dL/dm_i = sum_j lam_j . f(s_ij) d_ji,
+ * because m_i multiplies its pair term in every a_j.  Pairs beyond the cutoff
+ * contribute nothing (the step at r_c is not differentiated). */
+void ora_sr_force_adjoint(const double *x, const double *y, const double *z, const double *m,
+                          int64_t N, double L, double eps, double rcut, const double *c,
+                          const double *lx, const double *ly, const double *lz,
+                          const int64_t *targets, int64_t S,
+                          double *gx, double *gy, double *gz, double *gm)
+{
+    double rc2 = rcut * rcut;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < S; ++t) {
+        int64_t i = targets[t];
+        double xi = x[i], yi = y[i], zi = z[i], mi = m[i];
+        double li[3] = {lx[i], ly[i], lz[i]};
+        double g[3] = {0.0, 0.0, 0.0}, gmi = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double d[3];
+            d[0] = min_image(x[j] - xi, L);
+            d[1] = min_image(y[j] - yi, L);
+            d[2] = min_image(z[j] - zi, L);
+            double s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(s < rc2)) continue;
+            double f = ora_fsr(s, eps, c);
+            double fp = ora_dfsr(s, eps, c);
+            double mj = m[j];
+            double lj[3] = {lx[j], ly[j], lz[j]};
+            double dlj = d[0] * lj[0] + d[1] * lj[1] + d[2] * lj[2];
+            double dli = d[0] * li[0] + d[1] * li[1] + d[2] * li[2];
+            for (int a = 0; a < 3; ++a) {
+                double Jlj = f * lj[a] + 2.0 * fp * d[a] * dlj; /* J(d) lam_j */
+                double Jli = f * li[a] + 2.0 * fp * d[a] * dli; /* J(d) lam_i */
+                g[a] += mi * Jlj - mj * Jli;
+            }
+            /* d_ji = -d_ij */
+            gmi += -f * dlj;
+        }
+        gx[t] = g[0];
+        gy[t] = g[1];
+        gz[t] = g[2];
+        if (gm) gm[t] = gmi;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kick and drift (the kick/stream maps of Eq. 3's symplectic step)           */
+/* ------------------------------------------------------------------------ */
+
+/* v <- v + dt_k a ; then, if x != NULL, x <- x + dt_d v (with the new v),
+ * all in float64 on float64 arrays; no wrapping. */
+void ora_kick_drift(int64_t N, double *vx, double *vy, double *vz,
+                    const double *ax, const double *ay, const double *az, double dt_k,
+                    double *x, double *y, double *z, double dt_d)
+{
+    for (int64_t i = 0; i < N; ++i) {
+        vx[i] += dt_k * ax[i];
+        vy[i] += dt_k * ay[i];
+        vz[i] += dt_k * az[i];
+        if (x) {
+            x[i] += dt_d * vx[i];
+            y[i] += dt_d * vy[i];
+            z[i] += dt_d * vz[i];
+        }
+    }
+}

@@ -1,0 +1,407 @@
+"""Pins of the float64 CPU oracle against closed forms, invariants, library
+routines and brute force (no GPU).
+
+Each test is chosen so that a plausible slip in the oracle -- a dropped
+softening, a wrong sign of d, a swapped mass, a wrong polynomial index, a
+missing periodic image, an unstable sort, a missing neighbour cell -- fails.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import default_coeffs, fit_coeffs, gaussian_grid_force, uniform_box
+from synth import gridfit
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+EPS = 0.01
+RC = 3.0
+
+
+def _two(x1, x2, m1=1.0, m2=1.0, L=16.0):
+    x = np.array([x1[0], x2[0]])
+    y = np.array([x1[1], x2[1]])
+    z = np.array([x1[2], x2[2]])
+    return x, y, z, np.array([m1, m2]), L
+
+
+# --------------------------------------------------------------------------
+# force law
+# --------------------------------------------------------------------------
+
+def test_softened_newton_closed_form():
+    """c = 0: the law is softened Newtonian gravity truncated at r_c.
+
+    Textbook: a_1 = m_2 d / (r^2 + eps)^(3/2), d = x_2 - x_1 (attractive)."""
+    c = np.zeros(6)
+    for r, eps, m2 in [(1.0, 0.01, 2.5), (0.3, 0.5, 1.0), (2.9, 1e-6, 0.7)]:
+        x, y, z, m, L = _two((5.0, 5.0, 5.0), (5.0 + r, 5.0, 5.0), m1=1.3, m2=m2)
+        a = oracle.sr_force(x, y, z, m, L, eps, RC, c)
+        expect = m2 * r / (r * r + eps) ** 1.5
+        assert a[0, 0] == pytest.approx(expect, rel=1e-14)
+        assert a[0, 1] == 0.0 and a[0, 2] == 0.0
+        # particle 2 is pulled back towards particle 1 by m_1 (not m_2)
+        assert a[1, 0] == pytest.approx(-1.3 * r / (r * r + eps) ** 1.5, rel=1e-14)
+
+
+def test_newton_limit_inverse_square():
+    """eps -> 0, c = 0: |a| = m / r^2 (Newton)."""
+    c = np.zeros(6)
+    r = 1.7
+    x, y, z, m, L = _two((1.0, 2.0, 3.0), (1.0, 2.0 + r, 3.0), m2=3.0)
+    a = oracle.sr_force(x, y, z, m, L, 1e-300, RC, c)
+    assert np.linalg.norm(a[0]) == pytest.approx(3.0 / r ** 2, rel=1e-12)
+
+
+def test_polynomial_term_matches_numpy_polyval():
+    """The subtracted grid term equals numpy's polynomial evaluation.
+
+    Uses a random non-symmetric coefficient set so a wrong power or index
+    shows up; the Newtonian part is removed by differencing against c = 0."""
+    rng = np.random.default_rng(11)
+    c = rng.normal(size=6) * np.array([1, 0.3, 0.1, 0.03, 0.01, 0.003])
+    for r in [0.4, 1.1, 2.2, 2.95]:
+        s = r * r
+        x, y, z, m, L = _two((3.0, 3.0, 3.0), (3.0, 3.0, 3.0 + r), m2=1.0)
+        a_c = oracle.sr_force(x, y, z, m, L, EPS, RC, c)[0, 2]
+        a_0 = oracle.sr_force(x, y, z, m, L, EPS, RC, np.zeros(6))[0, 2]
+        assert (a_0 - a_c) / r == pytest.approx(np.polynomial.polynomial.polyval(s, c), rel=1e-12,
+                                                abs=1e-14)
+        # and the scalar helpers agree with the same definitions
+        assert oracle.fsr(s, EPS, c) == pytest.approx(a_c / r, rel=1e-12)
+        dnum = (oracle.fsr(s + 1e-6, EPS, c) - oracle.fsr(s - 1e-6, EPS, c)) / 2e-6
+        assert oracle.dfsr(s, EPS, c) == pytest.approx(dnum, rel=1e-6)
+
+
+def test_cutoff_is_exact_zero_and_strict():
+    c = default_coeffs().astype(np.float64)
+    # beyond the cutoff, and exactly at it (strict s < r_c^2)
+    for r in [3.0, 3.0001, 5.0, 7.9]:
+        x, y, z, m, L = _two((4.0, 4.0, 4.0), (4.0 + r, 4.0, 4.0))
+        a = oracle.sr_force(x, y, z, m, L, EPS, RC, c)
+        assert np.all(a == 0.0)
+    # isolated particle: exactly zero
+    a = oracle.sr_force(np.array([1.0]), np.array([1.0]), np.array([1.0]), np.array([1.0]),
+                        16.0, EPS, RC, c)
+    assert np.all(a == 0.0)
+
+
+def test_periodic_image_across_boundary():
+    """x = 0.5 and x = L - 0.5 are 1 apart through the boundary."""
+    c = default_coeffs().astype(np.float64)
+    L = 16.0
+    x, y, z, m, _ = _two((0.5, 8.0, 8.0), (L - 0.5, 8.0, 8.0))
+    a = oracle.sr_force(x, y, z, m, L, EPS, RC, c)
+    f1 = oracle.fsr(1.0, EPS, c)
+    assert f1 > 0
+    # particle 0 is pulled towards -x (through the boundary), particle 1 towards +x
+    assert a[0, 0] == pytest.approx(-f1, rel=1e-14)
+    assert a[1, 0] == pytest.approx(+f1, rel=1e-14)
+
+
+def test_newton_third_law_and_translation_invariance():
+    c = default_coeffs().astype(np.float64)
+    w = uniform_box(600, 8.0, seed=7)
+    rng = np.random.default_rng(3)
+    m = rng.uniform(0.5, 2.0, w.N)
+    a = oracle.sr_force(w.x, w.y, w.z, m, 8.0, EPS, RC, c)
+    mom = (m[:, None] * a).sum(0)
+    scale = (m[:, None] * np.abs(a)).sum()
+    assert np.all(np.abs(mom) < 1e-12 * scale)
+    shift = rng.uniform(0, 8.0, 3)
+    xs = np.mod(w.x.astype(np.float64) + shift[0], 8.0)
+    ys = np.mod(w.y.astype(np.float64) + shift[1], 8.0)
+    zs = np.mod(w.z.astype(np.float64) + shift[2], 8.0)
+    a2 = oracle.sr_force(xs, ys, zs, m, 8.0, EPS, RC, c)
+    assert np.max(np.abs(a2 - a)) < 1e-10 * np.max(np.abs(a))
+
+
+def test_superposition_and_mass_linearity():
+    c = default_coeffs().astype(np.float64)
+    pts = np.array([[4.0, 4.0, 4.0], [5.0, 4.5, 4.2], [3.1, 3.3, 5.0]])
+    m = np.array([1.0, 2.0, 0.5])
+    a = oracle.sr_force(pts[:, 0], pts[:, 1], pts[:, 2], m, 12.0, EPS, RC, c)
+    a01 = oracle.sr_force(pts[:2, 0], pts[:2, 1], pts[:2, 2], m[:2], 12.0, EPS, RC, c)
+    a02 = oracle.sr_force(pts[[0, 2], 0], pts[[0, 2], 1], pts[[0, 2], 2], m[[0, 2]], 12.0, EPS,
+                          RC, c)
+    assert np.allclose(a[0], a01[0] + a02[0], rtol=1e-14, atol=0)
+
+
+def test_perfect_lattice_has_zero_force():
+    """Every particle of a perfect periodic lattice feels no net force."""
+    c = default_coeffs().astype(np.float64)
+    g = np.arange(8) + 0.5
+    gz, gy, gx = np.meshgrid(g, g, g, indexing="ij")
+    a = oracle.sr_force(gx.ravel(), gy.ravel(), gz.ravel(), np.ones(512), 8.0, EPS, RC, c)
+    assert np.max(np.abs(a)) < 1e-12
+
+
+def test_brute_force_small_against_independent_numpy():
+    """Tiny N: a dense numpy evaluation (minimum image by rounding, masked sum)."""
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(5)
+    N, L = 40, 7.0
+    p = rng.random((N, 3)) * L
+    m = rng.uniform(0.5, 1.5, N)
+    a = oracle.sr_force(p[:, 0], p[:, 1], p[:, 2], m, L, EPS, RC, c)
+    d = p[None, :, :] - p[:, None, :]
+    d -= L * np.round(d / L)
+    s = (d * d).sum(-1)
+    mask = (s < RC * RC) & ~np.eye(N, dtype=bool)
+    f = np.where(mask, (s + EPS) ** -1.5 - np.polynomial.polynomial.polyval(s, c), 0.0)
+    ref = (m[None, :, None] * f[..., None] * d).sum(1)
+    assert np.allclose(a, ref, rtol=1e-12, atol=1e-12)
+    assert oracle.pair_count(p[:, 0], p[:, 1], p[:, 2], L, RC) == int(mask.sum())
+
+
+# --------------------------------------------------------------------------
+# adjoint
+# --------------------------------------------------------------------------
+
+def _pairs_clear_of_cutoff(p, L, margin):
+    d = p[None] - p[:, None]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(-1))
+    return np.all(np.abs(r - RC) > margin)
+
+
+def test_adjoint_against_finite_differences():
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(21)
+    L, N = 6.5, 48
+    while True:
+        p = rng.random((N, 3)) * L
+        if _pairs_clear_of_cutoff(p, L, 1e-3):
+            break
+    m = rng.uniform(0.5, 1.5, N)
+    lam = rng.normal(size=(N, 3))
+    gx, gm = oracle.sr_force_adjoint(p[:, 0], p[:, 1], p[:, 2], m, L, EPS, RC, c, lam)
+
+    def J(pp, mm):
+        a = oracle.sr_force(pp[:, 0], pp[:, 1], pp[:, 2], mm, L, EPS, RC, c)
+        return float((lam * a).sum())
+
+    h = 1e-6
+    for i in [0, 7, 31]:
+        for k in range(3):
+            pp, pm = p.copy(), p.copy()
+            pp[i, k] += h
+            pm[i, k] -= h
+            fd = (J(pp, m) - J(pm, m)) / (2 * h)
+            assert gx[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+        mp, mm = m.copy(), m.copy()
+        mp[i] += h
+        mm[i] -= h
+        fd = (J(p, mp) - J(p, mm)) / (2 * h)
+        assert gm[i] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_adjoint_against_torch_float64_autograd():
+    """Independent library check: float64 autograd of a dense expression."""
+    torch = pytest.importorskip("torch")
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(22)
+    L, N = 7.0, 96
+    p = rng.random((N, 3)) * L
+    m = rng.uniform(0.5, 1.5, N)
+    lam = rng.normal(size=(N, 3))
+    gx, gm = oracle.sr_force_adjoint(p[:, 0], p[:, 1], p[:, 2], m, L, EPS, RC, c, lam)
+
+    P = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    M = torch.tensor(m, dtype=torch.float64, requires_grad=True)
+    d = P[None, :, :] - P[:, None, :]
+    d = d - L * torch.round(d.detach() / L)
+    s = (d * d).sum(-1)
+    mask = (s < RC * RC) & ~torch.eye(N, dtype=torch.bool)
+    ss = torch.where(mask, s, torch.ones_like(s))
+    poly = sum(float(c[k]) * ss ** k for k in range(6))
+    f = torch.where(mask, (ss + EPS) ** -1.5 - poly, torch.zeros_like(s))
+    a = (M[None, :, None] * f[..., None] * d).sum(1)
+    (a * torch.tensor(lam)).sum().backward()
+    assert np.allclose(gx, P.grad.numpy(), rtol=1e-10, atol=1e-10)
+    assert np.allclose(gm, M.grad.numpy(), rtol=1e-10, atol=1e-10)
+
+
+def test_trajectory_gradient_against_finite_differences():
+    from oracle import diff
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(23)
+    L, N = 7.0, 40
+    while True:
+        x0 = rng.random((N, 3)) * L
+        if _pairs_clear_of_cutoff(x0, L, 2e-2):
+            break
+    v0 = rng.normal(scale=0.3, size=(N, 3))
+    m = rng.uniform(0.5, 1.5, N)
+    w = rng.normal(size=(N, 3))
+    dt, steps = 0.01, 4
+    gx, gv, gm = diff.gradient(x0, v0, m, L, EPS, RC, c, dt, steps, w)
+    h = 1e-5
+    for (i, k) in [(0, 0), (5, 1), (17, 2)]:
+        fd = diff.finite_difference(x0, v0, m, L, EPS, RC, c, dt, steps, w, "x", (i, k), h)
+        assert gx[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        fd = diff.finite_difference(x0, v0, m, L, EPS, RC, c, dt, steps, w, "v", (i, k), h)
+        assert gv[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    for i in [3, 11]:
+        fd = diff.finite_difference(x0, v0, m, L, EPS, RC, c, dt, steps, w, "m", i, h)
+        assert gm[i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_kick_drift_exact_on_dyadic_values():
+    v = np.array([[0.5, -0.25, 1.0]])
+    a = np.array([[2.0, 4.0, -8.0]])
+    x = np.array([[1.0, 2.0, 3.0]])
+    v2, x2 = oracle.kick_drift(v, a, 0.125, x, 0.5)
+    assert np.array_equal(v2, [[0.75, 0.25, 0.0]])
+    assert np.array_equal(x2, [[1.375, 2.125, 3.0]])
+
+
+# --------------------------------------------------------------------------
+# binning, lists, tasks
+# --------------------------------------------------------------------------
+
+def _wrap_f32_numpy(x, L):
+    """The binning's float32 wrap, restated with numpy float32 vector ops."""
+    x = x.astype(np.float32)
+    L = np.float32(L)
+    q = np.floor(x / L)
+    xw = x - q * L
+    xw = np.where(xw < 0, xw + L, xw)
+    xw = np.where(xw >= L, xw - L, xw)
+    return xw.astype(np.float32)
+
+
+def test_binning_invariants_and_numpy_restatement():
+    rng = np.random.default_rng(31)
+    L = np.float32(17.3)
+    N = 3000
+    x = (rng.random(N) * 3 * L - L).astype(np.float32)  # outside [0, L) too
+    y = (rng.random(N) * L).astype(np.float32)
+    z = (rng.normal(size=N) * 5).astype(np.float32)
+    x[:4] = [0.0, -0.0, L, np.nextafter(L, np.float32(0))]
+    x[4] = np.float32(-1e-9)
+    m = rng.uniform(0.5, 2, N).astype(np.float32)
+    b = oracle.bin_volume(x, y, z, m, float(L), 3.0)
+    n, w, iw = b["n"], b["w"], b["inv_w"]
+    assert n == 5 and w == np.float32(L / np.float32(5)) and iw == np.float32(np.float32(5) / L)
+    cs, perm, s4 = b["cell_start"], b["perm"], b["sorted4"]
+    assert cs[0] == 0 and cs[-1] == N and np.all(np.diff(cs) >= 0)
+    assert np.array_equal(np.sort(perm), np.arange(N))
+    # stable: ascending original index within each cell
+    for c in range(n ** 3):
+        seg = perm[cs[c]:cs[c + 1]]
+        assert np.all(np.diff(seg) > 0)
+        assert np.all(b["cell_of"][seg] == c)
+    # numpy float32 restatement of the cell definition, bit for bit
+    cells = []
+    wr = []
+    for arr in (x, y, z):
+        xw = _wrap_f32_numpy(arr, L)
+        assert np.all(xw >= 0) and np.all(xw < L)
+        cc = np.minimum(np.floor(xw * iw).astype(np.int64), n - 1)
+        cells.append(cc)
+        wr.append(xw)
+    cid = (cells[2] * n + cells[1]) * n + cells[0]
+    assert np.array_equal(cid, b["cell_of"])
+    for k, (cc, xw) in enumerate(zip(cells, wr)):
+        o = (xw - cc.astype(np.float32) * w).astype(np.float32)
+        assert np.array_equal(s4[:, k].view(np.int32), o[perm].view(np.int32))
+    assert np.array_equal(s4[:, 3], m[perm])
+    # offsets lie in the cell (to float32 rounding) and reproduce the position mod L
+    assert np.all(s4[:, :3] > -1e-5) and np.all(s4[:, :3] < w + 1e-5)
+    ccell = b["cell_of"][perm]
+    org = np.stack([ccell % n, (ccell // n) % n, ccell // (n * n)], 1) * np.float64(w)
+    pos = np.stack([x, y, z], 1)[perm].astype(np.float64)
+    diff = s4[:, :3].astype(np.float64) + org - pos
+    diff -= np.float64(L) * np.round(diff / np.float64(L))
+    assert np.max(np.abs(diff)) < 1e-5
+
+
+@pytest.mark.parametrize("L,cell_min,rcut", [(16.0, 3.0, 3.0), (10.0, 2.0, 3.0), (9.0, 3.0, 3.0),
+                                             (13.0, 1.4, 3.0)])
+def test_lists_cover_every_pair_within_cutoff(L, cell_min, rcut):
+    """Brute force: every pair closer than r_c is in a listed (cell, image)."""
+    rng = np.random.default_rng(41)
+    N = 900
+    p = (rng.random((N, 3)) * L).astype(np.float32)
+    m = np.ones(N, np.float32)
+    b = oracle.bin_volume(p[:, 0], p[:, 1], p[:, 2], m, L, cell_min)
+    n, w = b["n"], b["w"]
+    off, cell, shift = oracle.lists_volume(n, w, rcut)
+    listed = set()
+    for c in range(n ** 3):
+        for e in range(off[c], off[c + 1]):
+            listed.add((c, int(cell[e]), int(shift[e])))
+    # neighbour entries are distinct and the box distance predicate is tight
+    assert len(listed) == off[-1]
+    R = oracle.reach(w, rcut)
+    co = b["cell_of"]
+    d = p[None].astype(np.float64) - p[:, None].astype(np.float64)
+    img = np.round(d / L)
+    d -= L * img
+    s = (d * d).sum(-1)
+    ii, jj = np.nonzero((s < rcut * rcut) & ~np.eye(N, dtype=bool))
+    cx = lambda c: np.stack([c % n, (c // n) % n, c // (n * n)], -1)
+    for i, j in zip(ii, jj):
+        ci, cj = cx(co[i]), cx(co[j])
+        delta = cj - ci
+        # image that brings j next to i: the periodic offset of at most R cells
+        sh = np.zeros(3, int)
+        for a in range(3):
+            if delta[a] > R:
+                delta[a] -= n
+                sh[a] = -1
+            elif delta[a] < -R:
+                delta[a] += n
+                sh[a] = 1
+        code = (sh[2] + 1) * 9 + (sh[1] + 1) * 3 + (sh[0] + 1)
+        assert (int(co[i]), int(co[j]), code) in listed
+    if w >= rcut:
+        assert np.all(np.diff(off) == 27)
+
+
+def test_lists_reject_too_coarse_mesh():
+    with pytest.raises(ValueError):
+        oracle.lists_volume(4, 1.0, 3.0)   # R = 3 needs n >= 7
+
+
+def test_tasks_partition_each_cell():
+    w = uniform_box(2000, 12.0, seed=9)
+    b = oracle.bin_volume(w.x, w.y, w.z, w.m, 12.0, 3.0)
+    t = oracle.tasks(b["cell_start"], 7)
+    assert np.all(t[:, 2] - t[:, 1] <= 7) and np.all(t[:, 2] > t[:, 1])
+    assert t[0, 1] == 0 and t[-1, 2] == 2000 and np.all(t[1:, 1] == t[:-1, 2])
+    for c, s, e in t:
+        assert b["cell_start"][c] <= s < e <= b["cell_start"][c + 1]
+
+
+# --------------------------------------------------------------------------
+# grid-force fit (input generator of the coefficients)
+# --------------------------------------------------------------------------
+
+def test_gridfit_against_paper_constants_and_shell_theorem():
+    from scipy import integrate
+    consts = json.load(open(os.path.join(HERE, "golden", "paper_constants.json")))
+    sig, ns = consts["filter_sigma"]["value"], consts["filter_ns"]["value"]
+    se = gridfit.sigma_eff(sig, ns, 1.0)
+    assert se == pytest.approx(math.sqrt(0.64 + 7.0 / 6.0))
+    # shell theorem: g(r) r^3 = M(<r) of a 3-D Gaussian with per-axis std se/sqrt(2)
+    sg = se / math.sqrt(2.0)
+    rho = lambda r: 4 * math.pi * r * r * math.exp(-r * r / (2 * sg * sg)) / (2 * math.pi * sg * sg) ** 1.5
+    for r in [0.2, 1.0, 2.5, 4.0]:
+        M, _ = integrate.quad(rho, 0.0, r, epsabs=1e-14, epsrel=1e-12)
+        assert gaussian_grid_force(np.array([r * r]), se)[0] * r ** 3 == pytest.approx(M, rel=1e-9)
+    # small-r limit and large-r Newtonian asymptote
+    assert gaussian_grid_force(np.array([0.0]), se)[0] == pytest.approx(
+        4.0 / (3.0 * math.sqrt(math.pi) * se ** 3))
+    assert gaussian_grid_force(np.array([400.0]), se)[0] * 20.0 ** 3 == pytest.approx(1.0, rel=1e-12)
+    c = fit_coeffs(3.0, EPS)
+    assert len(c) == consts["poly_degree"]["value"] + 1
+    # continuity at the cutoff: f_SR(r_c^2) = 0
+    assert abs((9.0 + EPS) ** -1.5 - np.polynomial.polynomial.polyval(9.0, c)) < 1e-15
+    s = np.linspace(0, 9, 500)
+    assert np.max(np.abs(np.polynomial.polynomial.polyval(s, c) - gaussian_grid_force(s, se))) < 1e-3

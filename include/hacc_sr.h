@@ -1,0 +1,221 @@
+/*
+ * hacc_sr.h -- C ABI of the GB300 short-range particle-particle force path.
+ *
+ * The method is the short-range half of HACC's force split (Habib et al.,
+ * "The Universe at Extreme Scale: Multi-Petaflop Sky Simulation on the BG/Q",
+ * SC'12; arXiv:1211.4864):
+ *
+ *   a_i = sum_{j != i, s_ij < r_c^2} m_j f_SR(s_ij) d_ij,
+ *   f_SR(s) = (s + eps)^(-3/2) - poly[5](s),      s = d.d      (Eq. 4)
+ *
+ * where d_ij = x_j - x_i is the minimum periodic image, poly[5] is the
+ * fifth-order fit of the filtered grid force (Sec. II), eps the short-distance
+ * cutoff (softening, added to s) and r_c the matching radius of the force
+ * split (3 grid cells, Sec. II).  The paper evaluates it with an RCB tree and
+ * leaf-shared neighbour lists on the BG/Q (Sec. IV); this library bins the
+ * particles into a periodic chaining mesh (cell width >= the mesh's minimum
+ * width), builds per-cell neighbour-cell lists, evaluates the pair force on the
+ * GPU, and applies the kick of the split-operator step (Eq. 3).
+ *
+ * Conventions for every call
+ * --------------------------
+ *  * All array pointers are DEVICE pointers owned by the caller, unless the
+ *    comment says "host".  The library allocates no device memory: scratch
+ *    space is passed in as `ws` of at least the size that the matching
+ *    *_workspace_size query returns.  Float4 arrays (`sorted4`) and `ws` must
+ *    be 16-byte aligned.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls only enqueue work on it; nothing synchronises the host, so a
+ *    sequence of calls can be captured in a CUDA graph.
+ *  * Return value: HACC_OK, or a negative code for an error found on the host
+ *    (bad argument, CUDA launch error).  Errors that only the device can see
+ *    (a full task buffer, a wait that ran out, a non-finite coordinate) are
+ *    OR-ed as HACC_STATUS_* bits into the caller's device word `status`; read
+ *    it after the stream has finished.  No C++ exception crosses the ABI.
+ *  * Several volumes: every call works on V >= 1 independent periodic boxes
+ *    whose particles are concatenated; a one-box problem is V = 1.
+ *  * Particle counts are below 2^31.
+ */
+#ifndef HACC_SR_H
+#define HACC_SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HACC_OK 0
+#define HACC_ERR_INVALID (-1)  /* bad argument (checked on the host) */
+#define HACC_ERR_CAPACITY (-2) /* a buffer or workspace is too small */
+#define HACC_ERR_CUDA (-3)     /* a CUDA call failed */
+#define HACC_ERR_TIMEOUT (-4)  /* reserved for a host-side wait that ran out */
+
+/* bits of the device status word */
+#define HACC_STATUS_CAPACITY 1u /* task buffer too small: some tasks were dropped */
+#define HACC_STATUS_TIMEOUT 2u  /* a bounded device wait gave up; results invalid */
+#define HACC_STATUS_NONFINITE 4u /* a position was NaN or infinite (binned to 0) */
+
+/* One periodic volume of the chaining mesh (64 bytes).  Filled on the host by
+ * hacc_mesh_plan, then copied by the caller to device memory. */
+typedef struct hacc_volume {
+    int64_t p_begin;    /* first particle of this volume */
+    int64_t p_end;      /* one past its last particle */
+    int64_t cell_base;  /* global id of its first cell */
+    int64_t entry_base; /* index of its first neighbour-list entry */
+    int32_t n;          /* cells per side: floor(L / cell_min) */
+    int32_t R;          /* stencil reach in cells: ceil(r_c / w) */
+    int32_t S;          /* neighbour-list entries per cell */
+    float L;            /* box side (grid units) */
+    float w;            /* cell width, float32 L / n */
+    float inv_w;        /* float32 n / L, used to find a particle's cell */
+    float rcut;         /* cutoff the lists were planned for */
+    int32_t pad;
+} hacc_volume;
+
+/* Mesh of V volumes as the device calls see it. */
+typedef struct hacc_mesh {
+    const hacc_volume *vols; /* device [V] */
+    int32_t V;
+    int32_t pad;
+    int64_t N;         /* particles over all volumes (= vols[V-1].p_end) */
+    int64_t n_cells;   /* cells over all volumes */
+    int64_t n_entries; /* neighbour-list entries over all volumes */
+} hacc_mesh;
+
+/* Output of hacc_bin. */
+typedef struct hacc_binned {
+    int32_t *cell_of;    /* [N] global cell of particle i (input order) */
+    int32_t *cell_start; /* [n_cells + 1] first sorted slot of each cell */
+    int32_t *perm;       /* [N] input index of the particle in sorted slot k */
+    float *sorted4;      /* [4 N] per sorted slot (ox, oy, oz, m), o = cell-relative offset */
+} hacc_binned;
+
+/* Output of hacc_build_lists. */
+typedef struct hacc_lists {
+    int64_t *nbr_off;  /* [n_cells + 1] first entry of each cell's neighbour list */
+    int32_t *nbr_cell; /* [n_entries] global id of the neighbour cell */
+    int8_t *nbr_shift; /* [n_entries] periodic image: (sz+1)*9 + (sy+1)*3 + (sx+1) */
+    int32_t *tasks;    /* [4 task_cap] per task: cell, first slot, end slot, volume */
+    int32_t *n_tasks;  /* device scalar: number of tasks written */
+    int64_t *n_pairs;  /* device scalar: candidate ordered pairs (j != i) the force visits */
+    int64_t task_cap;  /* capacity of `tasks`, in tasks */
+    int32_t split_T;   /* a task holds at most split_T particles of one cell */
+    int32_t pad;
+} hacc_lists;
+
+/* Force-law parameters (host struct). */
+typedef struct hacc_sr_params {
+    float eps;  /* softening added to s (grid units^2), > 0 */
+    float rcut; /* cutoff radius r_c (grid units); pairs with s < r_c^2 interact */
+    float c[6]; /* poly[5] coefficients, poly(s) = sum_k c[k] s^k */
+} hacc_sr_params;
+
+/* Launch shape of the pair kernels (host struct; NULL = built-in default).
+ * The autotuner picks these per workload. */
+typedef struct hacc_launch {
+    int32_t warps_per_cta; /* 1..16 */
+    int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid, 1..8 */
+    int32_t jtile;         /* j particles per staged tile: 32, 64, 128 or 256 */
+    int32_t stages;        /* staged tiles in flight per warp: 2..4 */
+} hacc_launch;
+
+/* Library version and build target, e.g. "hacc_sr 1 sm_103a". Host. */
+const char *hacc_version(void);
+
+/* Plans the chaining mesh of V volumes (host only, no device work).
+ *   L[V]         host: box side of each volume (grid units), > 0
+ *   vol_off[V+1] host: particle ranges, vol_off[0] = 0, non-decreasing
+ *   cell_min     minimum cell width (normally r_c); n = floor(L / cell_min) >= 3
+ *   rcut         cutoff; requires L >= 2 r_c and n >= 2 R + 1 (unique image)
+ *   table[V]     host out: the volumes; copy it to the device for the calls
+ *   out_mesh     host out: totals (its `vols` is left NULL for the caller)
+ * The chaining mesh stands in for the paper's RCB tree (Sec. IV-A).
+ * Returns HACC_ERR_INVALID on any violated requirement. */
+int hacc_mesh_plan(int32_t V, const float *L, const int64_t *vol_off, float cell_min, float rcut,
+                   hacc_volume *table, hacc_mesh *out_mesh);
+
+/* Bytes of scratch that hacc_bin needs. */
+size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
+
+/* Bins the particles into the chaining mesh: the analogue of the paper's
+ * three-phase structure-of-arrays partition (Sec. IV-A), done as a stable
+ * counting sort.  For particle i of volume v, per axis: xw = x - L floor(x/L)
+ * (one correction step keeps xw in [0, L)), cell c = min(n-1, floor(xw inv_w)),
+ * offset o = xw - c w, each a single float32 round-to-nearest operation.
+ * Within a cell the sorted order is ascending input index (bit-exact and
+ * deterministic).  x, y, z, m: [N] input order.  Writes every array of `out`.
+ * A non-finite coordinate sets HACC_STATUS_NONFINITE and is binned as 0. */
+int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
+             const float *m, const hacc_binned *out, void *ws, size_t ws_bytes,
+             uint32_t *status, void *stream);
+
+/* Upper bound of the task count for split size T (host). */
+int64_t hacc_task_capacity(const hacc_mesh *mesh, int32_t split_T);
+
+/* Bytes of scratch that hacc_build_lists needs. */
+size_t hacc_lists_workspace_size(const hacc_mesh *mesh);
+
+/* Builds the per-cell neighbour-cell lists within the cutoff -- the
+ * analogue of the paper's tree walk producing leaf-shared interaction lists
+ * (Sec. IV-A, walk minimisation; every particle of a cell shares the cell's
+ * list, Sec. IV-B) -- and the task list.  A cell c' (with periodic image) is
+ * listed for cell c iff the two boxes can hold a pair closer than r_c:
+ * sum_a max(0, |delta_a| - 1)^2 w^2 < r_c^2 (float64), delta = integer cell
+ * offset; entries in ascending (dz, dy, dx).  Tasks cut each cell's sorted
+ * range into chunks of at most split_T particles, cells ascending.  Also
+ * counts the candidate pairs into *lists->n_pairs.  More tasks than task_cap
+ * sets HACC_STATUS_CAPACITY (the surplus is not written). */
+int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                     void *ws, size_t ws_bytes, uint32_t *status, void *stream);
+
+/* Bytes of scratch that hacc_sr_force / hacc_sr_force_adjoint need. */
+size_t hacc_force_workspace_size(const hacc_mesh *mesh);
+
+/* Short-range force (Eq. 4) on every particle, written to ax, ay, az [N] in
+ * input order (overwritten).  float32 arithmetic with the cutoff applied as a
+ * select inside the pair loop (the paper's fsel discussion, Sec. IV-B),
+ * rsqrt from the hardware unit, per-particle compensated accumulation.
+ * Requires eps > 0 (the softening keeps the self and coincident pairs
+ * finite) and p->rcut equal to the rcut the mesh was planned with. */
+int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                  const hacc_sr_params *p, float *ax, float *ay, float *az,
+                  const hacc_launch *launch, void *ws, size_t ws_bytes, uint32_t *status,
+                  void *stream);
+
+/* Vector-Jacobian product of hacc_sr_force (not in the paper).  Given
+ * lam = dL/da (gax, gay, gaz, [N] input order) returns, in input order,
+ *   gx_i = dL/dx_i = sum_j [m_i J(d_ij) lam_j - m_j J(d_ij) lam_i],
+ *   J(d) = f_SR(s) I + 2 f_SR'(s) d d^T,
+ *   gm_i = dL/dm_i = -sum_j f_SR(s_ij) d_ij . lam_j        (gm may be NULL),
+ * recomputing every pair term (nothing is stored by the forward call). */
+int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *binned,
+                          const hacc_lists *lists, const hacc_sr_params *p, const float *gax,
+                          const float *gay, const float *gaz, float *gx, float *gy, float *gz,
+                          float *gm, const hacc_launch *launch, void *ws, size_t ws_bytes,
+                          uint32_t *status, void *stream);
+
+/* Kick and optional drift of the split-operator step (Eq. 3):
+ *   v <- v + dt_kick a;  then, if x != NULL, x <- x + dt_drift v (new v),
+ * the drift computed in float64 and rounded once to float32.  If `mesh` is
+ * non-NULL the drifted positions are wrapped into [0, L) of their volume.
+ * Arrays [N] in input order; x, y, z may be NULL (kick only). */
+int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy, float *vz, const float *ax,
+              const float *ay, const float *az, float dt_kick, float *x, float *y, float *z,
+              float dt_drift, void *stream);
+
+/* Bytes of scratch that hacc_moments needs. */
+size_t hacc_moments_workspace_size(int64_t N);
+
+/* Global float64 reductions, in a fixed order (deterministic):
+ *   out[0..2] = sum m v,  out[3..5] = sum m a  (zero by Newton's third law),
+ *   out[6] = sum m |v|^2 / 2,  out[7] = sum m |a|.   out: device double[8]. */
+int hacc_moments(int64_t N, const float *m, const float *vx, const float *vy, const float *vz,
+                 const float *ax, const float *ay, const float *az, double *out, void *ws,
+                 size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HACC_SR_H */

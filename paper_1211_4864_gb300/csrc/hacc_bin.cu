@@ -1,0 +1,251 @@
+// Chaining-mesh binning: cell keys, stable LSD radix sort of (cell, index),
+// gather of cell-relative float4 (ox, oy, oz, m) into sorted order.
+//
+// The paper's tree build partitions structure-of-arrays particle data in three
+// phases (record, apply to six arrays, apply to the rest; Sec. IV-A) so that
+// streaming hides memory latency.  The GPU analogue is one streaming pass that
+// computes each particle's cell and its packed (offset, mass) record, a stable
+// radix sort that moves only 8-byte (key, index) pairs, and one gather of the
+// 16-byte records.
+#include "hacc_common.cuh"
+
+namespace hacc {
+namespace {
+
+constexpr int KEY_THREADS = 256;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int R_THREADS = 256;
+constexpr int R_WARPS = R_THREADS / 32;
+constexpr int R_ITEMS = 16;
+constexpr int R_TILE = R_THREADS * R_ITEMS;  // 4096 keys per block
+
+__device__ __forceinline__ float sanitize(float v, uint32_t *status)
+{
+    if (!isfinite(v)) {
+        atomicOr(status, HACC_STATUS_NONFINITE);
+        return 0.0f;
+    }
+    return v;
+}
+
+// Pass 1: per particle, its cell key, its (offset, mass) record in input
+// order, and the cell histogram.
+__global__ void __launch_bounds__(KEY_THREADS)
+k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *__restrict__ x,
+           const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ m,
+           int32_t *__restrict__ cell_of, int32_t *__restrict__ keys, float4 *__restrict__ rec,
+           int32_t *__restrict__ counts, uint32_t *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int v = find_volume_by_particle(vols, V, i);
+        const hacc_volume &vol = vols[v];
+        float L = vol.L, w = vol.w, iw = vol.inv_w;
+        int n = vol.n;
+        float xw = wrap32(sanitize(x[i], status), L);
+        float yw = wrap32(sanitize(y[i], status), L);
+        float zw = wrap32(sanitize(z[i], status), L);
+        int cx = cell1(xw, iw, n), cy = cell1(yw, iw, n), cz = cell1(zw, iw, n);
+        int32_t key = (int32_t)(vol.cell_base + ((int64_t)cz * n + cy) * n + cx);
+        cell_of[i] = key;
+        keys[i] = key;
+        float4 r;
+        r.x = __fsub_rn(xw, __fmul_rn((float)cx, w));
+        r.y = __fsub_rn(yw, __fmul_rn((float)cy, w));
+        r.z = __fsub_rn(zw, __fmul_rn((float)cz, w));
+        r.w = m[i];
+        rec[i] = r;
+        atomicAdd(&counts[key], 1);
+    }
+}
+
+// Radix pass, step 1: digit histogram of each 4096-key tile, digit-major.
+__global__ void __launch_bounds__(R_THREADS)
+k_radix_hist(const int32_t *__restrict__ keys, int64_t N, int shift, int nblk, int32_t *__restrict__ hist)
+{
+    __shared__ int32_t cnt[RADIX];
+    for (int d = threadIdx.x; d < RADIX; d += R_THREADS) cnt[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * R_TILE;
+#pragma unroll 4
+    for (int k = 0; k < R_ITEMS; ++k) {
+        int64_t i = base + (int64_t)k * R_THREADS + threadIdx.x;
+        if (i < N) atomicAdd(&cnt[((uint32_t)keys[i] >> shift) & (RADIX - 1)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += R_THREADS) hist[(int64_t)d * nblk + blockIdx.x] = cnt[d];
+}
+
+// Radix pass, step 2: stable scatter.  Warp w owns tile positions
+// [512 w, 512 w + 512), item k of lane l is position 512 w + 32 k + l, so
+// (warp, item, lane) order is input order; equal digits keep that order.
+__global__ void __launch_bounds__(R_THREADS)
+k_radix_scatter(const int32_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in, int64_t N,
+                int shift, int nblk, const int32_t *__restrict__ offs, int32_t *__restrict__ keys_out,
+                int32_t *__restrict__ vals_out)
+{
+    __shared__ int32_t wcnt[R_WARPS][RADIX + 1];
+    __shared__ int32_t base_d[RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < R_WARPS * (RADIX + 1); t += R_THREADS) (&wcnt[0][0])[t] = 0;
+    for (int d = threadIdx.x; d < RADIX; d += R_THREADS) base_d[d] = offs[(int64_t)d * nblk + blockIdx.x];
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int64_t p0 = (int64_t)blockIdx.x * R_TILE + warp * (32 * R_ITEMS) + lane;
+    int32_t key[R_ITEMS], rank[R_ITEMS];
+#pragma unroll
+    for (int k = 0; k < R_ITEMS; ++k) {
+        int64_t i = p0 + 32 * k;
+        bool valid = i < N;
+        key[k] = valid ? keys_in[i] : 0;
+        int d = valid ? (int)(((uint32_t)key[k] >> shift) & (RADIX - 1)) : RADIX;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        int cur = wcnt[warp][d];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) wcnt[warp][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[k] = cur + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < RADIX; d += R_THREADS) {
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < R_WARPS; ++w) {
+            int c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R_ITEMS; ++k) {
+        int64_t i = p0 + 32 * k;
+        if (i < N) {
+            int d = (int)(((uint32_t)key[k] >> shift) & (RADIX - 1));
+            int64_t pos = (int64_t)base_d[d] + wcnt[warp][d] + rank[k];
+            keys_out[pos] = key[k];
+            vals_out[pos] = vals_in ? vals_in[i] : (int32_t)i;
+        }
+    }
+}
+
+// Gather of the (offset, mass) records into sorted order.
+__global__ void __launch_bounds__(256)
+k_bin_gather(int64_t N, const int32_t *__restrict__ perm, const float4 *__restrict__ rec,
+             float4 *__restrict__ sorted4)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x)
+        sorted4[k] = rec[perm[k]];
+}
+
+struct BinWs {
+    int32_t *keys_a, *keys_b, *vals_a, *counts, *hist, *hist_off;
+    float4 *rec;
+    char *scan_ws;
+    size_t total;
+};
+
+int radix_blocks(int64_t N) { return (int)((N + R_TILE - 1) / R_TILE); }
+
+BinWs bin_ws_layout(const hacc_mesh *mesh, void *ws)
+{
+    BinWs b{};
+    char *p = reinterpret_cast<char *>(ws);
+    size_t off = 0;
+    int64_t N = mesh->N;
+    int nblk = radix_blocks(N);
+    int64_t nhist = (int64_t)RADIX * nblk;
+    auto take = [&](size_t bytes) {
+        char *q = p ? p + off : nullptr;
+        off += round_up(bytes, 256);
+        return q;
+    };
+    b.rec = reinterpret_cast<float4 *>(take((size_t)N * sizeof(float4)));
+    b.keys_a = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.keys_b = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.vals_a = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.counts = reinterpret_cast<int32_t *>(take((size_t)mesh->n_cells * 4));
+    b.hist = reinterpret_cast<int32_t *>(take((size_t)nhist * 4));
+    b.hist_off = reinterpret_cast<int32_t *>(take((size_t)(nhist + 1) * 4));
+    int64_t scan_n = nhist > mesh->n_cells ? nhist : mesh->n_cells;
+    b.scan_ws = take(scan_workspace_bytes(scan_n));
+    b.total = off;
+    return b;
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms() * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace hacc
+
+using namespace hacc;
+
+extern "C" size_t hacc_bin_workspace_size(const hacc_mesh *mesh)
+{
+    if (!mesh) return 0;
+    return bin_ws_layout(mesh, nullptr).total;
+}
+
+extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
+                        const float *m, const hacc_binned *out, void *ws, size_t ws_bytes,
+                        uint32_t *status, void *stream)
+{
+    if (!mesh || !out || !mesh->vols || mesh->V < 1 || mesh->N < 0 || !status) return HACC_ERR_INVALID;
+    if (!out->cell_start || !ws || !aligned16(ws)) return HACC_ERR_INVALID;
+    const int64_t N = mesh->N;
+    if (N > 0 && (!x || !y || !z || !m || !out->cell_of || !out->perm || !out->sorted4))
+        return HACC_ERR_INVALID;
+    if (N > 0 && !aligned16(out->sorted4)) return HACC_ERR_INVALID;
+    BinWs b = bin_ws_layout(mesh, ws);
+    if (ws_bytes < b.total) return HACC_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+
+    HACC_CUDA_TRY(cudaMemsetAsync(b.counts, 0, (size_t)mesh->n_cells * 4, st));
+    if (N > 0) {
+        k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(
+            mesh->vols, mesh->V, N, x, y, z, m, out->cell_of, b.keys_a, b.rec, b.counts, status);
+        HACC_LAUNCH_CHECK();
+    }
+    int rc = scan_exclusive_i32(b.counts, out->cell_start, mesh->n_cells, b.scan_ws, st);
+    if (rc) return rc;
+    if (N == 0) return HACC_OK;
+
+    // passes over the significant bits of the largest key
+    uint32_t maxkey = (uint32_t)(mesh->n_cells - 1);
+    int bits = 0;
+    while (bits < 32 && (maxkey >> bits) != 0) ++bits;
+    int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    if (passes < 1) passes = 1;
+    int nblk = radix_blocks(N);
+    int64_t nhist = (int64_t)RADIX * nblk;
+    // ping-pong so that the last pass writes its values into out->perm
+    int32_t *kin = b.keys_a, *vin = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        bool last = p == passes - 1;
+        int32_t *kout = (kin == b.keys_a) ? b.keys_b : b.keys_a;
+        // values alternate so that the final pass lands in out->perm
+        int32_t *vout = ((passes - 1 - p) % 2 == 0) ? out->perm : b.vals_a;
+        int shift = p * RADIX_BITS;
+        k_radix_hist<<<nblk, R_THREADS, 0, st>>>(kin, N, shift, nblk, b.hist);
+        HACC_LAUNCH_CHECK();
+        rc = scan_exclusive_i32(b.hist, b.hist_off, nhist, b.scan_ws, st);
+        if (rc) return rc;
+        k_radix_scatter<<<nblk, R_THREADS, 0, st>>>(kin, vin, N, shift, nblk, b.hist_off, kout, vout);
+        HACC_LAUNCH_CHECK();
+        (void)last;
+        kin = kout;
+        vin = vout;
+    }
+    k_bin_gather<<<grid_for(N, 256), 256, 0, st>>>(N, out->perm, b.rec,
+                                                   reinterpret_cast<float4 *>(out->sorted4));
+    HACC_LAUNCH_CHECK();
+    return HACC_OK;
+}

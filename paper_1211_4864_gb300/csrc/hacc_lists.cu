@@ -1,0 +1,195 @@
+// Per-cell neighbour-cell lists, task list and candidate-pair count.
+//
+// The paper's RCB tree walk builds one interaction list per leaf that every
+// particle of the leaf shares (walk minimisation, Sec. IV-A/B).  Here a cell
+// of the chaining mesh plays the leaf: its list holds the neighbour cells
+// (with their periodic image) whose boxes come closer than r_c.
+#include "hacc_common.cuh"
+
+namespace hacc {
+namespace {
+
+__device__ __forceinline__ void cell_coords(int64_t local, int n, int &cx, int &cy, int &cz)
+{
+    cx = (int)(local % n);
+    cy = (int)((local / n) % n);
+    cz = (int)(local / ((int64_t)n * n));
+}
+
+__global__ void __launch_bounds__(256)
+k_lists_fill(const hacc_volume *__restrict__ vols, int V, int64_t n_cells, int64_t n_entries,
+             int64_t *__restrict__ nbr_off, int32_t *__restrict__ nbr_cell, int8_t *__restrict__ nbr_shift,
+             uint32_t *status)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int v = find_volume_by_cell(vols, V, c);
+        const hacc_volume &vol = vols[v];
+        int n = vol.n, R = vol.R;
+        int64_t local = c - vol.cell_base;
+        int cx, cy, cz;
+        cell_coords(local, n, cx, cy, cz);
+        int64_t e = vol.entry_base + local * vol.S;
+        const int64_t e_end = e + vol.S;  // never write past this cell's planned slots
+        nbr_off[c] = e;
+        double w = (double)vol.w, rc = (double)vol.rcut;
+        for (int dz = -R; dz <= R; ++dz)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                    if (!cells_within(dx, dy, dz, w, rc)) continue;
+                    int px = cx + dx, py = cy + dy, pz = cz + dz;
+                    int sx = 0, sy = 0, sz = 0;
+                    if (px < 0) { px += n; sx = -1; } else if (px >= n) { px -= n; sx = 1; }
+                    if (py < 0) { py += n; sy = -1; } else if (py >= n) { py -= n; sy = 1; }
+                    if (pz < 0) { pz += n; sz = -1; } else if (pz >= n) { pz -= n; sz = 1; }
+                    if (e < e_end) {
+                        nbr_cell[e] = (int32_t)(vol.cell_base + ((int64_t)pz * n + py) * n + px);
+                        nbr_shift[e] = (int8_t)((sz + 1) * 9 + (sy + 1) * 3 + (sx + 1));
+                    }
+                    ++e;
+                }
+        if (e != e_end) atomicOr(status, HACC_STATUS_CAPACITY);
+        if (c == n_cells - 1) nbr_off[n_cells] = n_entries;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_task_counts(const int32_t *__restrict__ cell_start, int64_t n_cells, int T, int32_t *__restrict__ nt)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int cnt = cell_start[c + 1] - cell_start[c];
+        nt[c] = (cnt + T - 1) / T;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_task_fill(const hacc_volume *__restrict__ vols, int V, const int32_t *__restrict__ cell_start,
+            int64_t n_cells, int T, const int32_t *__restrict__ task_off, int64_t cap,
+            int4 *__restrict__ tasks)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int b = cell_start[c], e = cell_start[c + 1];
+        int64_t t = task_off[c];
+        int v = -1;
+        for (int i = b; i < e; i += T, ++t) {
+            if (t >= cap) break;
+            if (v < 0) v = find_volume_by_cell(vols, V, c);
+            tasks[t] = make_int4((int)c, i, (i + T < e) ? i + T : e, v);
+        }
+    }
+}
+
+// Candidate ordered pairs: sum over cells of count(c) * sum_list count(c').
+__global__ void __launch_bounds__(256)
+k_pair_count(const int32_t *__restrict__ cell_start, int64_t n_cells, const int64_t *__restrict__ nbr_off,
+             const int32_t *__restrict__ nbr_cell, unsigned long long *__restrict__ total)
+{
+    unsigned long long acc = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ni = cell_start[c + 1] - cell_start[c];
+        if (ni == 0) continue;
+        int64_t nj = 0;
+        for (int64_t e = nbr_off[c]; e < nbr_off[c + 1]; ++e) {
+            int cp = nbr_cell[e];
+            nj += cell_start[cp + 1] - cell_start[cp];
+        }
+        acc += (unsigned long long)(ni * nj);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+__global__ void k_lists_finish(const int32_t *__restrict__ task_off, int64_t n_cells, int64_t cap,
+                               int64_t N, int32_t *__restrict__ n_tasks, int64_t *__restrict__ n_pairs,
+                               uint32_t *status)
+{
+    int64_t total = task_off[n_cells];
+    if (total > cap) {
+        atomicOr(status, HACC_STATUS_CAPACITY);
+        total = cap;
+    }
+    *n_tasks = (int32_t)total;
+    if (n_pairs) *n_pairs -= N;  // each particle meets itself once in its own cell
+}
+
+struct ListWs {
+    int32_t *nt, *task_off;
+    char *scan_ws;
+    size_t total;
+};
+
+ListWs lists_layout(const hacc_mesh *mesh, void *ws)
+{
+    ListWs L{};
+    char *p = reinterpret_cast<char *>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *q = p ? p + off : nullptr;
+        off += round_up(bytes, 256);
+        return q;
+    };
+    L.nt = reinterpret_cast<int32_t *>(take((size_t)mesh->n_cells * 4));
+    L.task_off = reinterpret_cast<int32_t *>(take((size_t)(mesh->n_cells + 1) * 4));
+    L.scan_ws = take(scan_workspace_bytes(mesh->n_cells));
+    L.total = off;
+    return L;
+}
+
+int grid_cells(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * 16;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace hacc
+
+using namespace hacc;
+
+extern "C" size_t hacc_lists_workspace_size(const hacc_mesh *mesh)
+{
+    return mesh ? lists_layout(mesh, nullptr).total : 0;
+}
+
+extern "C" int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                                void *ws, size_t ws_bytes, uint32_t *status, void *stream)
+{
+    if (!mesh || !binned || !lists || !mesh->vols || !status || !ws) return HACC_ERR_INVALID;
+    if (!binned->cell_start || !lists->nbr_off || !lists->n_tasks || lists->split_T < 1 ||
+        lists->task_cap < 0)
+        return HACC_ERR_INVALID;
+    if (mesh->n_entries > 0 && (!lists->nbr_cell || !lists->nbr_shift)) return HACC_ERR_INVALID;
+    if (lists->task_cap > 0 && !lists->tasks) return HACC_ERR_INVALID;
+    if (!aligned16(lists->tasks)) return HACC_ERR_INVALID;
+    ListWs L = lists_layout(mesh, ws);
+    if (ws_bytes < L.total) return HACC_ERR_CAPACITY;
+    cudaStream_t st = as_stream(stream);
+    const int64_t nc = mesh->n_cells;
+    int g = grid_cells(nc);
+    k_lists_fill<<<g, 256, 0, st>>>(mesh->vols, mesh->V, nc, mesh->n_entries, lists->nbr_off,
+                                    lists->nbr_cell, lists->nbr_shift, status);
+    HACC_LAUNCH_CHECK();
+    k_task_counts<<<g, 256, 0, st>>>(binned->cell_start, nc, lists->split_T, L.nt);
+    HACC_LAUNCH_CHECK();
+    int rc = scan_exclusive_i32(L.nt, L.task_off, nc, L.scan_ws, st);
+    if (rc) return rc;
+    k_task_fill<<<g, 256, 0, st>>>(mesh->vols, mesh->V, binned->cell_start, nc, lists->split_T,
+                                   L.task_off, lists->task_cap, reinterpret_cast<int4 *>(lists->tasks));
+    HACC_LAUNCH_CHECK();
+    if (lists->n_pairs) {
+        HACC_CUDA_TRY(cudaMemsetAsync(lists->n_pairs, 0, sizeof(int64_t), st));
+        k_pair_count<<<g, 256, 0, st>>>(binned->cell_start, nc, lists->nbr_off, lists->nbr_cell,
+                                        reinterpret_cast<unsigned long long *>(lists->n_pairs));
+        HACC_LAUNCH_CHECK();
+    }
+    k_lists_finish<<<1, 1, 0, st>>>(L.task_off, nc, lists->task_cap, mesh->N, lists->n_tasks,
+                                    lists->n_pairs, status);
+    HACC_LAUNCH_CHECK();
+    return HACC_OK;
+}

@@ -1,0 +1,301 @@
+"""PyTorch-facing binding of the short-range force library.
+
+The functions named ``hacc_*`` mirror the C ABI one to one and only marshal
+arguments (torch tensors -> device pointers, the current CUDA stream).  The
+``ShortRange`` class owns the device buffers of one mesh (PyTorch allocates
+them) and sequences the calls; ``sr_force_autograd`` and ``kick_drift_autograd``
+wrap the calls as ``torch.autograd.Function``s whose backward passes call the
+hand-written adjoint and kick kernels.  No arithmetic of the method runs in
+Python or in PyTorch ops.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (HaccError, check, hacc_binned, hacc_launch, hacc_lists, hacc_mesh, hacc_sr_params,
+                   hacc_volume)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if t.numel() == 0:
+        return None
+    if not t.is_cuda:
+        raise HaccError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise HaccError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+@dataclass
+class SRParams:
+    """Force-law parameters: softening eps, cutoff rcut, poly[5] coefficients."""
+
+    eps: float
+    rcut: float
+    c: np.ndarray
+
+    def c_struct(self) -> hacc_sr_params:
+        p = hacc_sr_params()
+        p.eps = float(self.eps)
+        p.rcut = float(self.rcut)
+        cc = np.asarray(self.c, dtype=np.float32)
+        if cc.shape != (6,):
+            raise HaccError("need exactly six polynomial coefficients")
+        for k in range(6):
+            p.c[k] = float(cc[k])
+        return p
+
+
+@dataclass
+class Launch:
+    warps_per_cta: int = 8
+    ctas_per_sm: int = 2
+    jtile: int = 64
+    stages: int = 4
+
+    def c_struct(self) -> hacc_launch:
+        return hacc_launch(self.warps_per_cta, self.ctas_per_sm, self.jtile, self.stages)
+
+
+# ---------------------------------------------------------------------------
+# one-to-one wrappers of the C ABI
+# ---------------------------------------------------------------------------
+
+def hacc_version() -> str:
+    return _lib.load().hacc_version().decode()
+
+
+def hacc_mesh_plan(L, vol_off, cell_min: float, rcut: float):
+    """Host planning; returns (ctypes volume table, hacc_mesh)."""
+    L = np.ascontiguousarray(np.atleast_1d(L), dtype=np.float32)
+    vol_off = np.ascontiguousarray(vol_off, dtype=np.int64)
+    V = L.shape[0]
+    if vol_off.shape != (V + 1,):
+        raise HaccError("vol_off must have V + 1 entries")
+    table = (hacc_volume * V)()
+    mesh = hacc_mesh()
+    check(_lib.load().hacc_mesh_plan(V, L.ctypes.data, vol_off.ctypes.data, float(cell_min), float(rcut),
+                                     table, ctypes.byref(mesh)), "hacc_mesh_plan")
+    return table, mesh
+
+
+def hacc_bin(mesh, x, y, z, m, binned, ws, status):
+    check(_lib.load().hacc_bin(ctypes.byref(mesh), _ptr(x), _ptr(y), _ptr(z), _ptr(m), ctypes.byref(binned),
+                               _ptr(ws), ws.numel(), _ptr(status), _stream()), "hacc_bin")
+
+
+def hacc_build_lists(mesh, binned, lists, ws, status):
+    check(_lib.load().hacc_build_lists(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists), _ptr(ws),
+                                       ws.numel(), _ptr(status), _stream()), "hacc_build_lists")
+
+
+def hacc_sr_force(mesh, binned, lists, params: SRParams, ax, ay, az, ws, status, launch: Launch | None = None):
+    p = params.c_struct()
+    lc = launch.c_struct() if launch is not None else None
+    check(_lib.load().hacc_sr_force(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists), ctypes.byref(p),
+                                    _ptr(ax), _ptr(ay), _ptr(az), ctypes.byref(lc) if lc else None, _ptr(ws),
+                                    ws.numel(), _ptr(status), _stream()), "hacc_sr_force")
+
+
+def hacc_sr_force_adjoint(mesh, binned, lists, params: SRParams, gax, gay, gaz, gx, gy, gz, gm, ws, status,
+                          launch: Launch | None = None):
+    p = params.c_struct()
+    lc = launch.c_struct() if launch is not None else None
+    check(_lib.load().hacc_sr_force_adjoint(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
+                                            ctypes.byref(p), _ptr(gax), _ptr(gay), _ptr(gaz), _ptr(gx), _ptr(gy),
+                                            _ptr(gz), _ptr(gm), ctypes.byref(lc) if lc else None, _ptr(ws),
+                                            ws.numel(), _ptr(status), _stream()), "hacc_sr_force_adjoint")
+
+
+def hacc_kick(mesh, N, vx, vy, vz, ax, ay, az, dt_kick, x=None, y=None, z=None, dt_drift=0.0):
+    check(_lib.load().hacc_kick(ctypes.byref(mesh) if mesh is not None else None, int(N), _ptr(vx), _ptr(vy),
+                                _ptr(vz), _ptr(ax), _ptr(ay), _ptr(az), float(dt_kick), _ptr(x), _ptr(y), _ptr(z),
+                                float(dt_drift), _stream()), "hacc_kick")
+
+
+def hacc_moments(N, m, vx, vy, vz, ax, ay, az, out, ws):
+    check(_lib.load().hacc_moments(int(N), _ptr(m), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(ax), _ptr(ay), _ptr(az),
+                                   _ptr(out), _ptr(ws), ws.numel(), _stream()), "hacc_moments")
+
+
+# ---------------------------------------------------------------------------
+# buffers of one mesh
+# ---------------------------------------------------------------------------
+
+class ShortRange:
+    """Device buffers and the call sequence for one chaining mesh of V volumes.
+
+    ``L`` (per volume box sides) and ``vol_off`` (particle ranges) are host
+    arrays; positions, masses, velocities and accelerations are float32 CUDA
+    tensors of length N in input order.
+    """
+
+    def __init__(self, L, vol_off, rcut: float, cell_min: float | None = None, split_T: int = 32,
+                 device: str | torch.device = "cuda"):
+        self.device = torch.device(device)
+        self.rcut = float(rcut)
+        self.cell_min = float(cell_min if cell_min is not None else rcut)
+        self.table, self.mesh = hacc_mesh_plan(L, vol_off, self.cell_min, self.rcut)
+        self.V = int(self.mesh.V)
+        self.N = int(self.mesh.N)
+        self.n_cells = int(self.mesh.n_cells)
+        self.n_entries = int(self.mesh.n_entries)
+        raw = bytes(self.table)
+        self.vols = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(self.device)
+        self.mesh.vols = self.vols.data_ptr()
+        lib = _lib.load()
+        dev = self.device
+        i32, i64 = torch.int32, torch.int64
+        N = self.N
+        self.cell_of = torch.empty(N, dtype=i32, device=dev)
+        self.cell_start = torch.empty(self.n_cells + 1, dtype=i32, device=dev)
+        self.perm = torch.empty(N, dtype=i32, device=dev)
+        self.sorted4 = torch.empty((N, 4), dtype=torch.float32, device=dev)
+        self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.cell_start), _ptr(self.perm), _ptr(self.sorted4))
+        self.split_T = int(split_T)
+        self.task_cap = int(lib.hacc_task_capacity(ctypes.byref(self.mesh), self.split_T))
+        self.nbr_off = torch.empty(self.n_cells + 1, dtype=i64, device=dev)
+        self.nbr_cell = torch.empty(self.n_entries, dtype=i32, device=dev)
+        self.nbr_shift = torch.empty(self.n_entries, dtype=torch.int8, device=dev)
+        self.tasks = torch.empty((max(self.task_cap, 1), 4), dtype=i32, device=dev)
+        self.n_tasks = torch.zeros(1, dtype=i32, device=dev)
+        self.n_pairs = torch.zeros(1, dtype=i64, device=dev)
+        self.lists = hacc_lists(_ptr(self.nbr_off), _ptr(self.nbr_cell), _ptr(self.nbr_shift), _ptr(self.tasks),
+                                _ptr(self.n_tasks), _ptr(self.n_pairs), self.task_cap, self.split_T, 0)
+        ws_bytes = max(lib.hacc_bin_workspace_size(ctypes.byref(self.mesh)),
+                       lib.hacc_lists_workspace_size(ctypes.byref(self.mesh)),
+                       lib.hacc_force_workspace_size(ctypes.byref(self.mesh)),
+                       lib.hacc_moments_workspace_size(N))
+        self.ws = torch.empty(int(ws_bytes), dtype=torch.uint8, device=dev)
+        self.status = torch.zeros(1, dtype=i32, device=dev)
+
+    # -- calls ------------------------------------------------------------
+    def bin(self, x, y, z, m):
+        hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status)
+
+    def build_lists(self):
+        hacc_build_lists(self.mesh, self.binned, self.lists, self.ws, self.status)
+
+    def force(self, params: SRParams, out=None, launch: Launch | None = None):
+        if out is None:
+            out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
+        hacc_sr_force(self.mesh, self.binned, self.lists, params, out[0], out[1], out[2], self.ws, self.status,
+                      launch)
+        return out
+
+    def adjoint(self, params: SRParams, lam, out=None, want_gm: bool = True, launch: Launch | None = None):
+        """lam: [3, N] cotangent of the accelerations; returns (gx [3, N], gm [N] or None)."""
+        if out is None:
+            out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
+        gm = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_gm else None
+        lam = lam.contiguous()
+        hacc_sr_force_adjoint(self.mesh, self.binned, self.lists, params, lam[0], lam[1], lam[2], out[0], out[1],
+                              out[2], gm, self.ws, self.status, launch)
+        return out, gm
+
+    def kick(self, v, a, dt_kick, pos=None, dt_drift=0.0, wrap=True):
+        """v += dt_kick a; then pos += dt_drift v (wrapped into the boxes if wrap)."""
+        if pos is None:
+            hacc_kick(None, self.N, v[0], v[1], v[2], a[0], a[1], a[2], dt_kick)
+        else:
+            hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], a[0], a[1], a[2], dt_kick, pos[0],
+                      pos[1], pos[2], dt_drift)
+
+    def moments(self, m, v=None, a=None):
+        out = torch.empty(8, dtype=torch.float64, device=self.device)
+        vx = vy = vz = ax = ay = az = None
+        if v is not None:
+            vx, vy, vz = v[0], v[1], v[2]
+        if a is not None:
+            ax, ay, az = a[0], a[1], a[2]
+        hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.ws)
+        return out
+
+    def prepare(self, pos, m):
+        """Binning and lists for positions pos [3, N] and masses m [N]."""
+        self.bin(pos[0], pos[1], pos[2], m)
+        self.build_lists()
+
+    def check_status(self):
+        s = int(self.status.item())
+        if s:
+            self.status.zero_()
+            raise HaccError(f"device status {s:#x}")
+
+    def pair_count(self) -> int:
+        return int(self.n_pairs.item())
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+
+class _SRForce(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pos, m, solver: ShortRange, params: SRParams):
+        solver.prepare(pos, m)
+        a = solver.force(params)
+        ctx.save_for_backward(pos, m)
+        ctx.solver = solver
+        ctx.params = params
+        return a
+
+    @staticmethod
+    def backward(ctx, ga):
+        pos, m = ctx.saved_tensors
+        solver = ctx.solver
+        # the pair terms are recomputed: re-bin the saved positions, then the adjoint
+        solver.prepare(pos, m)
+        gpos, gm = solver.adjoint(ctx.params, ga.contiguous(), want_gm=ctx.needs_input_grad[1])
+        return gpos, gm, None, None
+
+
+class _KickDrift(torch.autograd.Function):
+    """v' = v + dt_k a ; x' = x + dt_d v' (no wrap), forward and VJP by hacc_kick."""
+
+    @staticmethod
+    def forward(ctx, v, pos, a, dt_k: float, dt_d: float):
+        v2 = v.clone()
+        p2 = pos.clone()
+        N = v.shape[1]
+        hacc_kick(None, N, v2[0], v2[1], v2[2], a[0], a[1], a[2], dt_k, p2[0], p2[1], p2[2], dt_d)
+        ctx.dt = (dt_k, dt_d)
+        return v2, p2
+
+    @staticmethod
+    def backward(ctx, gv2, gp2):
+        dt_k, dt_d = ctx.dt
+        if gv2 is None:
+            gv2 = torch.zeros_like(gp2)
+        if gp2 is None:
+            gp2 = torch.zeros_like(gv2)
+        gp2 = gp2.contiguous()
+        gv = gv2.contiguous().clone()
+        N = gv.shape[1]
+        # gv = gv' + dt_d gx'   (v' feeds x')
+        hacc_kick(None, N, gv[0], gv[1], gv[2], gp2[0], gp2[1], gp2[2], dt_d)
+        # ga = dt_k gv
+        ga = torch.zeros_like(gv)
+        hacc_kick(None, N, ga[0], ga[1], ga[2], gv[0], gv[1], gv[2], dt_k)
+        return gv, gp2, ga, None, None
+
+
+def sr_force_autograd(pos, m, solver: ShortRange, params: SRParams):
+    """Accelerations [3, N] of positions pos [3, N]; differentiable in pos and m."""
+    return _SRForce.apply(pos.contiguous(), m.contiguous(), solver, params)
+
+
+def kick_drift_autograd(v, pos, a, dt_k: float, dt_d: float):
+    return _KickDrift.apply(v.contiguous(), pos.contiguous(), a.contiguous(), dt_k, dt_d)

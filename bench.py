@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range force path on GB300.
+
+One step = the whole hot path on one synthetic workload resident in HBM:
+chaining-mesh binning -> neighbour lists and tasks -> pair force -> kick ->
+float64 moments (momentum, Newton-III residual, kinetic energy).  The metric
+is candidate pair interactions per second (the ordered pairs j != i that the
+force kernel evaluates, counted by the list builder), whole job over all
+ranks.  Default workload: 256^3 = 16,777,216 particles, 60 % uniform and 40 %
+in 2000 NFW halos, box 256, r_c = 3, eps = 0.01 (the clustered configuration
+the throughput target is stated on).
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the float64 CPU
+oracle on bounded samples of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
+METRIC = "short-range pair interactions/s"
+UNIT = "pairs/s"
+WORKLOADS = {
+    "clustered256": "256^3 = 16,777,216 particles, L = 256, 60% uniform + 40% in 2000 NFW halos "
+                    "(log-uniform masses, c = 5-10, seed 3), r_c = 3, eps = 0.01, cell_min = 3, one force "
+                    "evaluation + kick per step",
+    "lattice128": "128^3 = 2,097,152 particles, L = 128, unit lattice + Gaussian displacement rms 0.5 "
+                  "(seed 2), r_c = 3, eps = 0.01, cell_min = 3, one force evaluation + kick per step",
+    "batched256": "256 periodic sub-volumes, 4k-256k particles each (log-uniform, seed 5), half uniform "
+                  "and half clustered, r_c = 3, eps = 0.01; bin + lists + force + kick of all volumes",
+    "uniform4096": "4096 uniform particles, L = 16, r_c = 3, eps = 0.01",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="clustered256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle error check")
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle target particles in the CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# ranks
+# ---------------------------------------------------------------------------
+
+class Ranks:
+    """torchrun ranks (RANK / WORLD_SIZE / MASTER_* from the environment)."""
+
+    def __init__(self, backend: str):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if self.world > 1 and not dist.is_initialized():
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([f.strip() for f in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def tuned_launch(hs, config: str):
+    from paper_1211_4864_gb300 import autotune
+    return autotune.cached(config)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1211_4864_gb300 as hs
+    from synth import default_coeffs, make_config
+
+    ranks = Ranks("nccl")
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    hs.load()
+    w = make_config(args.config)
+    prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
+    launch = tuned_launch(hs, args.config)
+    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=32, device=dev)
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device=dev)
+    m = torch.tensor(w.m, device=dev)
+    v0 = torch.tensor(np.stack([w.vx, w.vy, w.vz]), device=dev)
+    v = v0.clone()
+    a = torch.empty_like(v)
+    mom = None
+    stream = torch.cuda.current_stream()
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def step(k=None):
+        nonlocal mom
+        sr.prepare(pos, m)
+        if k is not None:
+            f0[k].record(stream)
+        sr.force(prm, a, launch=launch)
+        if k is not None:
+            f1[k].record(stream)
+        sr.kick(v, a, w.dt)
+        mom = sr.moments(m, v, a)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    sr.check_status()
+    pairs = sr.pair_count()
+
+    clocks = ClockSampler(ranks.local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = hs.hacc_kernel_launches()
+    ranks.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    launches = hs.hacc_kernel_launches() - launches0
+    clk = clocks.stop()
+    sr.check_status()
+    t_ms = e0.elapsed_time(e1)
+    t_ms_max = ranks.max(t_ms)
+    t_force = statistics.mean(f0[k].elapsed_time(f1[k]) for k in range(args.steps))
+    total_pairs = ranks.sum(float(pairs)) * args.steps
+    value = total_pairs / (t_ms_max * 1e-3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "N": w.N, "volumes": w.V,
+                      "pairs_per_step": pairs, "replicas": ranks.world,
+                      "l2": "inputs larger than L2 (sorted float4 268 MB + SoA positions 201 MB for "
+                            "clustered256); no flush between steps",
+                      "launch": launch.__dict__ if launch else "default",
+                      "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
+           "gpu_launches": int(launches), "clocks": clk}
+
+    # roofline of the dominant kernel (the pair force): plain FP32 ALU bound
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * 128 * 2 * f_max * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": "k_pairs<FORCE> (hacc_sr_force)", "achieved": achieved,
+                       "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                       "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (max SM clock)",
+                       "flops_per_pair": FLOPS_PER_PAIR, "force_ms": t_force,
+                       "force_share": t_force / (t_ms / args.steps)}
+    if clk.get("sm_mhz"):
+        out["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    # forward + adjoint on the same lists (not part of the timed step)
+    lam = torch.randn((3, w.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    sr.prepare(pos, m)
+    sr.adjoint(prm, lam, want_gm=False, launch=launch)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(3):
+        sr.adjoint(prm, lam, want_gm=False, launch=launch)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    t_adj = ea.elapsed_time(eb) / 3
+    out["fwd_adjoint"] = {"force_ms": t_force, "adjoint_ms": t_adj, "ratio_fwd_plus_adj_over_fwd":
+                          (t_force + t_adj) / t_force}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs)
+
+    # sampled float64 oracle check of this run's forces (untimed)
+    if not args.no_check and ranks.rank == 0:
+        out["error_vs_oracle"] = check_sample(sr, pos, m, prm, w, launch)
+
+    if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, prm, args.cpu_sample)
+    if ranks.rank == 0:
+        print(json.dumps(out), flush=True)
+    ranks.close()
+
+
+def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
+    """Same step with inputs in pinned host memory, copies inside the timed region."""
+    host_in = torch.tensor(np.stack([w.x, w.y, w.z, w.m, w.vx, w.vy, w.vz]).astype(np.float32)).pin_memory()
+    host_out = torch.empty((3, w.N), dtype=torch.float32).pin_memory()
+    host_mom = torch.empty(8, dtype=torch.float64).pin_memory()
+    dbuf = torch.empty((7, w.N), dtype=torch.float32, device=dev)
+    a = torch.empty((3, w.N), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dbuf.copy_(host_in, non_blocking=True)
+        pos = dbuf[0:3]
+        m = dbuf[3]
+        v = dbuf[4:7]
+        sr.prepare(pos, m)
+        sr.force(prm, a, launch=launch)
+        sr.kick(v, a, w.dt)
+        mom = sr.moments(m, v, a)
+        host_out.copy_(v, non_blocking=True)
+        host_mom.copy_(mom, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ranks.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t = ranks.max(e0.elapsed_time(e1))
+    total = ranks.sum(float(pairs)) * args.steps
+    return {"value": total / (t * 1e-3), "unit": UNIT, "ms_per_step": t / args.steps,
+            "h2d_bytes_per_step": int(host_in.numel() * 4),
+            "d2h_bytes_per_step": int(host_out.numel() * 4 + host_mom.numel() * 8)}
+
+
+def check_sample(sr, pos, m, prm, w, launch, S=256):
+    import torch
+
+    import oracle
+    if w.V != 1:
+        return None
+    a = sr.force(prm, launch=launch)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    tg = rng.choice(w.N, size=min(S, w.N), replace=False)
+    ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    got = a.cpu().numpy().T[tg].astype(np.float64)
+    num = np.linalg.norm(got - ref)
+    mag = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt(np.mean(mag * mag))
+    per = np.linalg.norm(got - ref, axis=1) / np.maximum(mag, floor)
+    return {"targets": int(len(tg)), "rms_rel": float(num / np.linalg.norm(ref)), "max_rel": float(per.max()),
+            "reference": "float64 brute force over all N sources"}
+
+
+def cpu_baseline(w, prm, S):
+    """The float64 oracle on a bounded sample of the same workload (all host cores)."""
+    import oracle
+    rng = np.random.default_rng(12)
+    tg = rng.choice(w.N, size=min(S, w.N), replace=False)
+    x, y, z, m = (np.ascontiguousarray(q, dtype=np.float64) for q in (w.x, w.y, w.z, w.m))
+    t = time.perf_counter()
+    oracle.sr_force(x, y, z, m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    dt = time.perf_counter() - t
+    evals = len(tg) * (w.N - 1)
+    return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(tg)} seeded target particles x all {w.N - 1} sources (brute force, float64), "
+                      f"{dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ranks = Ranks("gloo")
+    if ranks.rank != 0:
+        ranks.close()
+        return
+    import oracle
+    from synth import default_coeffs, make_config
+    w = make_config(args.config)
+    c = default_coeffs(w.rcut, w.eps).astype(np.float64)
+    b, e = int(w.vol_off[0]), int(w.vol_off[1])
+    x, y, z, m = (np.ascontiguousarray(q[b:e], dtype=np.float64) for q in (w.x, w.y, w.z, w.m))
+    n = e - b
+    S = 256 if n > 1_000_000 else min(n, 4096)
+    rng = np.random.default_rng(13)
+
+    def one():
+        tg = rng.choice(n, size=S, replace=False)
+        oracle.sr_force(x, y, z, m, float(w.L[0]), w.eps, w.rcut, c, tg)
+
+    for _ in range(args.warmup):
+        one()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t
+    value = S * (n - 1) * args.steps / dt
+    sample = (f"per step {S} seeded target particles x all {n - 1} sources of volume 0 "
+              f"(float64 brute force)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    ranks.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,6 +124,10 @@ typedef struct hacc_launch {
 /* Library version and build target, e.g. "hacc_sr 1 sm_103a". Host. */
 const char *hacc_version(void);
 
+/* Number of kernels this library has launched in this process so far (host;
+ * a tracing aid: the difference across a region counts its launches). */
+uint64_t hacc_kernel_launches(void);
+
 /* Plans the chaining mesh of V volumes (host only, no device work).
  *   L[V]         host: box side of each volume (grid units), > 0
  *   vol_off[V+1] host: particle ranges, vol_off[0] = 0, non-decreasing

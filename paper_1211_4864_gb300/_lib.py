@@ -69,6 +69,7 @@ _PS = ctypes.POINTER
 # name -> (restype, argtypes); the order of the header
 SIGNATURES = {
     "hacc_version": (ctypes.c_char_p, []),
+    "hacc_kernel_launches": (ctypes.c_uint64, []),
     "hacc_mesh_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_float, ctypes.c_float,
                                       _PS(hacc_volume), _PS(hacc_mesh)]),
     "hacc_bin_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh)]),

@@ -12,8 +12,10 @@
         if (err__ != cudaSuccess) return HACC_ERR_CUDA;       \
     } while (0)
 
+// After every kernel launch: count it, and turn a launch error into a code.
 #define HACC_LAUNCH_CHECK()                                   \
     do {                                                      \
+        hacc::count_launch();                                 \
         if (cudaPeekAtLastError() != cudaSuccess) {           \
             (void)cudaGetLastError();                         \
             return HACC_ERR_CUDA;                             \
@@ -21,6 +23,9 @@
     } while (0)
 
 namespace hacc {
+
+// Process-wide count of kernels this library has launched (hacc_kernel_launches).
+void count_launch();
 
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -1,5 +1,7 @@
 // Deterministic exclusive prefix sum of int32 counts (reduce-then-scan).
 // Used for cell starts, task offsets and radix-sort digit offsets.
+#include <atomic>
+
 #include "hacc_common.cuh"
 
 namespace hacc {
@@ -139,6 +141,12 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, cud
     return scan_level(in, out, n, 1, reinterpret_cast<char *>(ws), st);
 }
 
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
 int num_sms()
 {
     int dev = 0, sms = 0;
@@ -148,3 +156,5 @@ int num_sms()
 }
 
 }  // namespace hacc
+
+extern "C" uint64_t hacc_kernel_launches(void) { return hacc::launches(); }

@@ -77,6 +77,10 @@ def hacc_version() -> str:
     return _lib.load().hacc_version().decode()
 
 
+def hacc_kernel_launches() -> int:
+    return int(_lib.load().hacc_kernel_launches())
+
+
 def hacc_mesh_plan(L, vol_off, cell_min: float, rcut: float):
     """Host planning; returns (ctypes volume table, hacc_mesh)."""
     L = np.ascontiguousarray(np.atleast_1d(L), dtype=np.float32)

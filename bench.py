@@ -163,9 +163,10 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 
-def tuned_launch(hs, config: str):
+def tuned(config: str):
+    """(launch shape, split threshold) from the autotuner's cache, if tuned."""
     from paper_1211_4864_gb300 import autotune
-    return autotune.cached(config)
+    return autotune.cached(config), autotune.cached_split(config, default=64), autotune.cached(config, "adjoint")
 
 
 def run_ours(args):
@@ -180,8 +181,8 @@ def run_ours(args):
     hs.load()
     w = make_config(args.config)
     prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
-    launch = tuned_launch(hs, args.config)
-    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=32, device=dev)
+    launch, split_T, launch_adj = tuned(args.config)
+    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=split_T, device=dev)
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device=dev)
     m = torch.tensor(w.m, device=dev)
     v0 = torch.tensor(np.stack([w.vx, w.vy, w.vz]), device=dev)
@@ -239,7 +240,7 @@ def run_ours(args):
                       "pairs_per_step": pairs, "replicas": ranks.world,
                       "l2": "inputs larger than L2 (sorted float4 268 MB + SoA positions 201 MB for "
                             "clustered256); no flush between steps",
-                      "launch": launch.__dict__ if launch else "default",
+                      "launch": launch.__dict__ if launch else "default", "split_T": split_T,
                       "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
            "gpu_launches": int(launches), "clocks": clk}
 
@@ -265,12 +266,12 @@ def run_ours(args):
     # forward + adjoint on the same lists (not part of the timed step)
     lam = torch.randn((3, w.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
     sr.prepare(pos, m)
-    sr.adjoint(prm, lam, want_gm=False, launch=launch)
+    sr.adjoint(prm, lam, want_gm=False, launch=launch_adj)
     torch.cuda.synchronize()
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ea.record(stream)
     for _ in range(3):
-        sr.adjoint(prm, lam, want_gm=False, launch=launch)
+        sr.adjoint(prm, lam, want_gm=False, launch=launch_adj)
     eb.record(stream)
     torch.cuda.synchronize()
     t_adj = ea.elapsed_time(eb) / 3

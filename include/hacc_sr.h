@@ -100,6 +100,8 @@ typedef struct hacc_lists {
     int32_t *tasks;    /* [4 task_cap] per task: cell, first slot, end slot, volume */
     int32_t *n_tasks;  /* device scalar: number of tasks written */
     int64_t *n_pairs;  /* device scalar: candidate ordered pairs (j != i) the force visits */
+    int32_t *task_order; /* [task_cap] the order the pair kernels take tasks in: by descending
+                            cost class (particles x list length, power-of-two classes), stable */
     int64_t task_cap;  /* capacity of `tasks`, in tasks */
     int32_t split_T;   /* a task holds at most split_T particles of one cell */
     int32_t pad;
@@ -115,7 +117,7 @@ typedef struct hacc_sr_params {
 /* Launch shape of the pair kernels (host struct; NULL = built-in default).
  * The autotuner picks these per workload. */
 typedef struct hacc_launch {
-    int32_t warps_per_cta; /* 1..16 */
+    int32_t warps_per_cta; /* 1..8 */
     int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid, 1..8 */
     int32_t jtile;         /* j particles per staged tile: 32, 64, 128 or 256 */
     int32_t stages;        /* staged tiles in flight per warp: 2..4 */
@@ -168,7 +170,9 @@ size_t hacc_lists_workspace_size(const hacc_mesh *mesh);
  * listed for cell c iff the two boxes can hold a pair closer than r_c:
  * sum_a max(0, |delta_a| - 1)^2 w^2 < r_c^2 (float64), delta = integer cell
  * offset; entries in ascending (dz, dy, dx).  Tasks cut each cell's sorted
- * range into chunks of at most split_T particles, cells ascending.  Also
+ * range into chunks of at most split_T particles, cells ascending; task_order
+ * lists them heaviest first (so that the persistent pair kernels do not end
+ * on a long halo task), ties in cell order.  Also
  * counts the candidate pairs into *lists->n_pairs.  More tasks than task_cap
  * sets HACC_STATUS_CAPACITY (the surplus is not written). */
 int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,

@@ -49,7 +49,7 @@ class hacc_binned(ctypes.Structure):
 class hacc_lists(ctypes.Structure):
     _fields_ = [("nbr_off", ctypes.c_void_p), ("nbr_cell", ctypes.c_void_p), ("nbr_shift", ctypes.c_void_p),
                 ("tasks", ctypes.c_void_p), ("n_tasks", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p),
-                ("task_cap", ctypes.c_int64), ("split_T", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("task_order", ctypes.c_void_p), ("task_cap", ctypes.c_int64), ("split_T", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class hacc_sr_params(ctypes.Structure):

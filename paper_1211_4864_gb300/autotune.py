@@ -25,14 +25,14 @@ TILE_STAGES = [(32, 2), (32, 4), (64, 2), (64, 3), (64, 4), (128, 2), (128, 3), 
 
 
 def candidates(quick: bool = False):
-    warps = [4, 8, 16]
-    per_sm = [1, 2, 3, 4]
+    warps = [4, 8]
+    per_sm = [1, 2, 3, 4, 6]
     ts = TILE_STAGES
     if quick:
         warps, per_sm, ts = [4, 8], [2, 3], [(32, 4), (64, 4), (128, 2), (128, 4)]
     out = []
     for w, c, (jt, st) in itertools.product(warps, per_sm, ts):
-        if w * c > 48:  # more resident warps than an SM holds
+        if w * c > 32:  # more warps than the kernel's 80 registers let an SM hold
             continue
         out.append(Launch(w, c, jt, st))
     return out
@@ -62,12 +62,18 @@ def cached(config: str, mode: str = "force", path: str = CACHE) -> Launch | None
     return Launch(**ent["launch"])
 
 
+def cached_split(config: str, default: int = 64, path: str = CACHE) -> int:
+    """The split threshold (particles per task) chosen for a workload."""
+    ent = load_cache(path).get(_key(config), {}).get("force")
+    return int(ent.get("split_T", default)) if ent else default
+
+
 def tune(run, config: str, mode: str = "force", quick: bool = False, reps: int = 3, path: str = CACHE,
-         write: bool = True):
+         write: bool = True, extra: dict | None = None, cands=None):
     """Time ``run(launch)`` for every candidate; returns (best Launch, table)."""
     import torch
     table = []
-    for L in candidates(quick):
+    for L in (cands if cands is not None else candidates(quick)):
         try:
             run(L)
             torch.cuda.synchronize()
@@ -88,7 +94,62 @@ def tune(run, config: str, mode: str = "force", quick: bool = False, reps: int =
     if write:
         cache = load_cache(path)
         ent = cache.setdefault(_key(config), {})
-        ent[mode] = {"launch": best[0].__dict__, "ms": best[1], "candidates": len(ok)}
+        ent[mode] = {"launch": best[0].__dict__, "ms": best[1], "candidates": len(ok), **(extra or {})}
         with open(path, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
     return best[0], table
+
+
+def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str = CACHE) -> dict:
+    """Tune split threshold and launch shape of the force and adjoint kernels
+    on one of the standard workloads (synth.make_config names)."""
+    import numpy as np
+    import torch
+
+    from synth import default_coeffs, make_config
+
+    from .sr import ShortRange, SRParams
+
+    w = make_config(config)
+    prm = SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    m = torch.tensor(w.m, device="cuda")
+    best = None
+    report = {}
+    for T in splits:
+        sr = ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
+        sr.prepare(pos, m)
+        out = torch.empty((3, w.N), device="cuda")
+        L, table = tune(lambda L: sr.force(prm, out, launch=L), config, quick=quick, write=False)
+        ms = min(t[1] for t in table if t[1] is not None)
+        report[T] = [(t[0].__dict__, t[1]) for t in table]
+        if best is None or ms < best[2]:
+            best = (T, L, ms, sr)
+        del sr
+        torch.cuda.empty_cache()
+    T, L, ms, sr = best
+    cache = load_cache(path)
+    ent = cache.setdefault(_key(config), {})
+    ent["force"] = {"launch": L.__dict__, "ms": ms, "split_T": T}
+    lam = torch.randn((3, w.N), device="cuda")
+    La, _ = tune(lambda L: sr.adjoint(prm, lam, want_gm=False, launch=L), config, mode="adjoint", quick=True,
+                 write=False)
+    ent["adjoint"] = {"launch": La.__dict__}
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    return {"best": ent, "table": report}
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="tune split threshold and launch shape per workload")
+    ap.add_argument("configs", nargs="*", default=["clustered256"])
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--out", default=CACHE, help="cache file to update")
+    args = ap.parse_args()
+    for name in args.configs:
+        res = tune_workload(name, quick=args.quick, path=args.out)
+        print(name, json.dumps(res["best"]))
+        for T, rows in res["table"].items():
+            for L, ms in sorted(rows, key=lambda r: (r[1] is None, r[1] or 0))[:8]:
+                print(f"  T={T} {L} {ms}")

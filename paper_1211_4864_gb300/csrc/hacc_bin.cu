@@ -141,9 +141,9 @@ k_bin_gather(int64_t N, const int32_t *__restrict__ perm, const float4 *__restri
 }
 
 struct BinWs {
-    int32_t *keys_a, *keys_b, *vals_a, *counts, *hist, *hist_off;
+    int32_t *keys, *counts;
     float4 *rec;
-    char *scan_ws;
+    char *scan_ws, *sort_ws;
     size_t total;
 };
 
@@ -155,25 +155,68 @@ BinWs bin_ws_layout(const hacc_mesh *mesh, void *ws)
     char *p = reinterpret_cast<char *>(ws);
     size_t off = 0;
     int64_t N = mesh->N;
-    int nblk = radix_blocks(N);
-    int64_t nhist = (int64_t)RADIX * nblk;
     auto take = [&](size_t bytes) {
         char *q = p ? p + off : nullptr;
         off += round_up(bytes, 256);
         return q;
     };
     b.rec = reinterpret_cast<float4 *>(take((size_t)N * sizeof(float4)));
-    b.keys_a = reinterpret_cast<int32_t *>(take((size_t)N * 4));
-    b.keys_b = reinterpret_cast<int32_t *>(take((size_t)N * 4));
-    b.vals_a = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.keys = reinterpret_cast<int32_t *>(take((size_t)N * 4));
     b.counts = reinterpret_cast<int32_t *>(take((size_t)mesh->n_cells * 4));
-    b.hist = reinterpret_cast<int32_t *>(take((size_t)nhist * 4));
-    b.hist_off = reinterpret_cast<int32_t *>(take((size_t)(nhist + 1) * 4));
-    int64_t scan_n = nhist > mesh->n_cells ? nhist : mesh->n_cells;
-    b.scan_ws = take(scan_workspace_bytes(scan_n));
+    b.scan_ws = take(scan_workspace_bytes(mesh->n_cells));
+    b.sort_ws = take(sort_workspace_bytes(N));
     b.total = off;
     return b;
 }
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t N)
+{
+    const int64_t nhist = (int64_t)RADIX * radix_blocks(N);
+    return round_up((size_t)N * 4, 256) * 3 + round_up((size_t)nhist * 4, 256) +
+           round_up((size_t)(nhist + 1) * 4, 256) + scan_workspace_bytes(nhist);
+}
+
+int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st)
+{
+    if (N <= 0) return HACC_OK;
+    char *p = reinterpret_cast<char *>(ws);
+    const int nblk = radix_blocks(N);
+    const int64_t nhist = (int64_t)RADIX * nblk;
+    int32_t *keys_a = reinterpret_cast<int32_t *>(p);
+    p += round_up((size_t)N * 4, 256);
+    int32_t *keys_b = reinterpret_cast<int32_t *>(p);
+    p += round_up((size_t)N * 4, 256);
+    int32_t *vals_a = reinterpret_cast<int32_t *>(p);
+    p += round_up((size_t)N * 4, 256);
+    int32_t *hist = reinterpret_cast<int32_t *>(p);
+    p += round_up((size_t)nhist * 4, 256);
+    int32_t *hist_off = reinterpret_cast<int32_t *>(p);
+    p += round_up((size_t)(nhist + 1) * 4, 256);
+    char *scan_ws = p;
+    int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
+    if (passes < 1) passes = 1;
+    const int32_t *kin = keys;
+    const int32_t *vin = nullptr;  // first pass: values are the indices themselves
+    for (int pass = 0; pass < passes; ++pass) {
+        int32_t *kout = (pass % 2 == 0) ? keys_a : keys_b;
+        // values alternate so that the final pass lands in `order`
+        int32_t *vout = ((passes - 1 - pass) % 2 == 0) ? order : vals_a;
+        const int shift = pass * RADIX_BITS;
+        k_radix_hist<<<nblk, R_THREADS, 0, st>>>(kin, N, shift, nblk, hist);
+        HACC_LAUNCH_CHECK();
+        int rc = scan_exclusive_i32(hist, hist_off, nhist, scan_ws, st);
+        if (rc) return rc;
+        k_radix_scatter<<<nblk, R_THREADS, 0, st>>>(kin, vin, N, shift, nblk, hist_off, kout, vout);
+        HACC_LAUNCH_CHECK();
+        kin = kout;
+        vin = vout;
+    }
+    return HACC_OK;
+}
+
+namespace {
 
 int grid_for(int64_t n, int threads)
 {
@@ -211,39 +254,19 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     HACC_CUDA_TRY(cudaMemsetAsync(b.counts, 0, (size_t)mesh->n_cells * 4, st));
     if (N > 0) {
         k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(
-            mesh->vols, mesh->V, N, x, y, z, m, out->cell_of, b.keys_a, b.rec, b.counts, status);
+            mesh->vols, mesh->V, N, x, y, z, m, out->cell_of, b.keys, b.rec, b.counts, status);
         HACC_LAUNCH_CHECK();
     }
     int rc = scan_exclusive_i32(b.counts, out->cell_start, mesh->n_cells, b.scan_ws, st);
     if (rc) return rc;
     if (N == 0) return HACC_OK;
 
-    // passes over the significant bits of the largest key
-    uint32_t maxkey = (uint32_t)(mesh->n_cells - 1);
+    // stable sort of the particle indices by cell: perm
+    const uint32_t maxkey = (uint32_t)(mesh->n_cells - 1);
     int bits = 0;
     while (bits < 32 && (maxkey >> bits) != 0) ++bits;
-    int passes = (bits + RADIX_BITS - 1) / RADIX_BITS;
-    if (passes < 1) passes = 1;
-    int nblk = radix_blocks(N);
-    int64_t nhist = (int64_t)RADIX * nblk;
-    // ping-pong so that the last pass writes its values into out->perm
-    int32_t *kin = b.keys_a, *vin = nullptr;
-    for (int p = 0; p < passes; ++p) {
-        bool last = p == passes - 1;
-        int32_t *kout = (kin == b.keys_a) ? b.keys_b : b.keys_a;
-        // values alternate so that the final pass lands in out->perm
-        int32_t *vout = ((passes - 1 - p) % 2 == 0) ? out->perm : b.vals_a;
-        int shift = p * RADIX_BITS;
-        k_radix_hist<<<nblk, R_THREADS, 0, st>>>(kin, N, shift, nblk, b.hist);
-        HACC_LAUNCH_CHECK();
-        rc = scan_exclusive_i32(b.hist, b.hist_off, nhist, b.scan_ws, st);
-        if (rc) return rc;
-        k_radix_scatter<<<nblk, R_THREADS, 0, st>>>(kin, vin, N, shift, nblk, b.hist_off, kout, vout);
-        HACC_LAUNCH_CHECK();
-        (void)last;
-        kin = kout;
-        vin = vout;
-    }
+    rc = sort_index_stable(b.keys, N, bits, out->perm, b.sort_ws, st);
+    if (rc) return rc;
     k_bin_gather<<<grid_for(N, 256), 256, 0, st>>>(N, out->perm, b.rec,
                                                    reinterpret_cast<float4 *>(out->sorted4));
     HACC_LAUNCH_CHECK();

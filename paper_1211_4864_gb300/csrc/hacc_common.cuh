@@ -97,4 +97,10 @@ __host__ __device__ __forceinline__ bool cells_within(int dx, int dy, int dz, do
 size_t scan_workspace_bytes(int64_t n);
 int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, cudaStream_t st);
 
+// Stable sort of indices by int32 key (LSD radix, 8-bit digits, only the low
+// `bits` bits significant): order[k] = index of the k-th smallest key, ties
+// in index order.  ws: sort_workspace_bytes(N).  Deterministic.
+size_t sort_workspace_bytes(int64_t N);
+int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st);
+
 }  // namespace hacc

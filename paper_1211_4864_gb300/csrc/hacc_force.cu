@@ -29,6 +29,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+constexpr uint32_t WAIT_HINT_NS = 100000;  // a waiting warp may sleep up to 0.1 ms per try
 
 enum Mode { FORCE = 0, ADJOINT = 1 };
 
@@ -46,6 +47,7 @@ struct KArgs {
     const int32_t *nbr_cell;
     const int8_t *nbr_shift;
     const int4 *tasks;
+    const int32_t *order;  // task_order: heaviest first
     const int32_t *n_tasks;
     const float4 *pos;   // sorted (ox, oy, oz, m)
     const float4 *lam;   // sorted (lx, ly, lz, 0), adjoint only
@@ -71,10 +73,10 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(WAIT_HINT_NS)
         : "memory");
     return ok;
 }
@@ -137,24 +139,36 @@ __device__ __forceinline__ bool next_tile(int ng, int cnt, int &k, int &off, int
     return false;
 }
 
-template <int MODE>
+// Per-lane accumulators of IPL i particles: float32 within a tile, then
+// folded into a compensated (hi, lo) pair.
+template <int MODE, int IPL>
 struct Acc;
 
-template <>
-struct Acc<FORCE> {
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+template <int IPL>
+struct Acc<FORCE, IPL> {
+    float a[IPL][3], h[IPL][3], l[IPL][3];
+    __device__ __forceinline__ Acc()
+    {
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a[u][k] = h[u][k] = l[u][k] = 0.f;
+    }
     __device__ __forceinline__ void fold()
     {
-        two_sum_acc(hx, lx, ax);
-        two_sum_acc(hy, ly, ay);
-        two_sum_acc(hz, lz, az);
-        ax = ay = az = 0.f;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                two_sum_acc(h[u][k], l[u][k], a[u][k]);
+                a[u][k] = 0.f;
+            }
     }
 };
 
-template <>
-struct Acc<ADJOINT> {
+template <int IPL>
+struct Acc<ADJOINT, IPL> {
+    static_assert(IPL == 1, "the adjoint runs one i particle per lane");
     float u[3] = {0.f, 0.f, 0.f}, x[3] = {0.f, 0.f, 0.f}, v = 0.f, g = 0.f;
     float hu[3] = {0.f, 0.f, 0.f}, lu[3] = {0.f, 0.f, 0.f};
     float hx[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
@@ -162,11 +176,11 @@ struct Acc<ADJOINT> {
     __device__ __forceinline__ void fold()
     {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            two_sum_acc(hu[a], lu[a], u[a]);
-            two_sum_acc(hx[a], lx[a], x[a]);
-            u[a] = 0.f;
-            x[a] = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            two_sum_acc(hu[k], lu[k], u[k]);
+            two_sum_acc(hx[k], lx[k], x[k]);
+            u[k] = 0.f;
+            x[k] = 0.f;
         }
         two_sum_acc(hv, lv, v);
         two_sum_acc(hg, lg, g);
@@ -175,25 +189,55 @@ struct Acc<ADJOINT> {
     }
 };
 
-// Forward pair loop over one staged tile.
-__device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n, float oxp, float oyp,
-                                           float ozp, const PairConsts &K, Acc<FORCE> &A)
+// Hardware reciprocal square root (MUFU) without the denormal-input fix-up
+// that rsqrtf() adds: its argument s + eps is at least eps, a normal float.
+__device__ __forceinline__ float rsqrt_hw(float x)
 {
-#pragma unroll 4
-    for (int j = 0; j < n; ++j) {
-        float4 p = tj[j];
-        float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
-        float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
-        float t = rsqrtf(se);
-        float t2 = t * t;
-        float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
-                       K.nc[0]);
-        float f = fmaf(t2, t, q);
-        f = se < K.rc2e ? f : 0.0f;
-        float g = f * p.w;
-        A.ax = fmaf(g, dx, A.ax);
-        A.ay = fmaf(g, dy, A.ay);
-        A.az = fmaf(g, dz, A.az);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One pair of the forward law, accumulated into acc[3].  The cutoff test is
+// a compare whose predicate guards the three accumulating fma (no branch, no
+// select): the paper folds the same test into the loop with fsel (Sec. IV-B).
+__device__ __forceinline__ void pair_force(const float4 p, float oxp, float oyp, float ozp, const PairConsts &K,
+                                           float *acc)
+{
+    float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
+    float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
+    float t = rsqrt_hw(se);
+    float t2 = t * t;
+    float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
+                   K.nc[0]);
+    float g = fmaf(t2, t, q) * p.w;
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %3, %4;\n\t"
+        "@p fma.rn.f32 %0, %5, %6, %0;\n\t@p fma.rn.f32 %1, %5, %7, %1;\n\t@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
+        : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2])
+        : "f"(se), "f"(K.rc2e), "f"(g), "f"(dx), "f"(dy), "f"(dz));
+}
+
+// Forward pair loop over one staged tile: every staged j meets the IPL i
+// particles of this lane.  Unrolled by hand, four j per trip.
+template <int IPL>
+__device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n, const float (&op)[IPL][3],
+                                           const PairConsts &K, Acc<FORCE, IPL> &A)
+{
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+        const float4 p0 = tj[j], p1 = tj[j + 1], p2 = tj[j + 2], p3 = tj[j + 3];
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            pair_force(p0, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force(p1, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force(p2, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force(p3, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+        }
+    }
+    for (; j < n; ++j) {
+        const float4 p = tj[j];
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) pair_force(p, op[u][0], op[u][1], op[u][2], K, A.a[u]);
     }
 }
 
@@ -201,39 +245,46 @@ __device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n,
 // fp2 = 2 f_SR'(s):  U += f lam_j ;  V += m_j f ;
 // X += fp2 (m_i (d.lam_j) - m_j (d.lam_i)) d ;  G += f (d.lam_j).
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
+__device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, float oxp, float oyp, float ozp,
+                                             float mi, float lix, float liy, float liz, const PairConsts &K,
+                                             Acc<ADJOINT, 1> &A)
+{
+    float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
+    float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
+    float t = rsqrt_hw(se);
+    float t2 = t * t;
+    float t3 = t2 * t;
+    float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
+                   K.nc[0]);
+    float f = t3 + q;
+    float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
+    float fp2 = fmaf(-3.0f, t3 * t2, qp);
+    float dlj = fmaf(dz, l.z, fmaf(dy, l.y, dx * l.x));
+    float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
+    float r = fp2 * fmaf(mi, dlj, -(p.w * dli));
+    // the eight accumulations of this pair happen only inside the cutoff
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
+        "@p fma.rn.f32 %0, %10, %11, %0;\n\t@p fma.rn.f32 %1, %10, %12, %1;\n\t@p fma.rn.f32 %2, %10, %13, %2;\n\t"
+        "@p fma.rn.f32 %3, %14, %10, %3;\n\t"
+        "@p fma.rn.f32 %4, %15, %16, %4;\n\t@p fma.rn.f32 %5, %15, %17, %5;\n\t@p fma.rn.f32 %6, %15, %18, %6;\n\t"
+        "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
+        : "+f"(A.u[0]), "+f"(A.u[1]), "+f"(A.u[2]), "+f"(A.v), "+f"(A.x[0]), "+f"(A.x[1]), "+f"(A.x[2]),
+          "+f"(A.g)
+        : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
+          "f"(dz), "f"(dlj));
+}
+
 __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, const float4 *__restrict__ tl, int n,
                                              float oxp, float oyp, float ozp, float mi, float lix, float liy,
-                                             float liz, const PairConsts &K, Acc<ADJOINT> &A)
+                                             float liz, const PairConsts &K, Acc<ADJOINT, 1> &A)
 {
-#pragma unroll 2
-    for (int j = 0; j < n; ++j) {
-        float4 p = tj[j];
-        float4 l = tl[j];
-        float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
-        float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
-        float t = rsqrtf(se);
-        float t2 = t * t;
-        float t3 = t2 * t;
-        float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
-                       K.nc[0]);
-        float f = t3 + q;
-        float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
-        float fp2 = fmaf(-3.0f, t3 * t2, qp);
-        bool in = se < K.rc2e;
-        f = in ? f : 0.0f;
-        fp2 = in ? fp2 : 0.0f;
-        float dlj = fmaf(dz, l.z, fmaf(dy, l.y, dx * l.x));
-        float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
-        A.u[0] = fmaf(f, l.x, A.u[0]);
-        A.u[1] = fmaf(f, l.y, A.u[1]);
-        A.u[2] = fmaf(f, l.z, A.u[2]);
-        A.v = fmaf(p.w, f, A.v);
-        float r = fp2 * fmaf(mi, dlj, -(p.w * dli));
-        A.x[0] = fmaf(r, dx, A.x[0]);
-        A.x[1] = fmaf(r, dy, A.x[1]);
-        A.x[2] = fmaf(r, dz, A.x[2]);
-        A.g = fmaf(f, dlj, A.g);
+    int j = 0;
+    for (; j + 2 <= n; j += 2) {
+        const float4 p0 = tj[j], p1 = tj[j + 1], l0 = tl[j], l1 = tl[j + 1];
+        pair_adjoint(p0, l0, oxp, oyp, ozp, mi, lix, liy, liz, K, A);
+        pair_adjoint(p1, l1, oxp, oyp, ozp, mi, lix, liy, liz, K, A);
     }
+    if (j < n) pair_adjoint(tj[j], tl[j], oxp, oyp, ozp, mi, lix, liy, liz, K, A);
 }
 
 // Shared memory of one warp: STAGES tiles (two arrays in the adjoint) and
@@ -243,147 +294,191 @@ __host__ __device__ constexpr int warp_smem_bytes(int mode, int jt, int stages)
     return ((stages * (mode == ADJOINT ? 2 : 1) * jt * 16 + stages * 8) + 127) / 128 * 128;
 }
 
+// Per-warp staging ring: STAGES tiles, their mbarriers and the lifetime tile
+// counters (tile t lives in stage t % STAGES, phase parity (t / STAGES) & 1).
 template <int MODE, int JT, int STAGES>
-__global__ void __launch_bounds__(512) k_pairs(const KArgs a)
+struct Ring {
+    static constexpr int NBUF = MODE == ADJOINT ? 2 : 1;
+    float4 *tiles;
+    uint64_t *bars;
+    uint32_t issued = 0, consumed = 0;
+    __device__ __forceinline__ float4 *tile(uint32_t st) const { return tiles + (size_t)st * NBUF * JT; }
+    __device__ __forceinline__ uint32_t bar(uint32_t st) const { return smem_addr(&bars[st]); }
+    // lane 0 starts the copy of n records at j (positions, plus cotangents in the adjoint)
+    __device__ __forceinline__ void issue(const KArgs &a, int lane, int j, int n)
+    {
+        if (lane == 0) {
+            const uint32_t st = issued % STAGES;
+            tma_issue(bar(st), smem_addr(tile(st)), a.pos + j, (uint32_t)n * 16u, smem_addr(tile(st) + JT),
+                      MODE == ADJOINT ? (const void *)(a.lam + j) : nullptr);
+        }
+        ++issued;
+    }
+    // bounded wait for the next tile; false if the wait ran out
+    __device__ __forceinline__ bool wait_next() const
+    {
+        const uint32_t st = consumed % STAGES;
+        return warp_wait(bar(st), (consumed / STAGES) & 1u);
+    }
+    // after a timeout: let the copies still in flight land (bounded) before leaving
+    __device__ __forceinline__ void drain()
+    {
+        while (consumed < issued) {
+            warp_wait(bar(consumed % STAGES), (consumed / STAGES) & 1u);
+            ++consumed;
+        }
+    }
+};
+
+// One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
+// entry of the cell's neighbour list.  Returns false if a wait ran out.
+template <int MODE, int JT, int STAGES, int IPL>
+__device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> &ring, int lane, int c, int ib,
+                                         int ie, const hacc_volume &vol)
+{
+    const PairConsts &K = a.k;
+    const int n = vol.n;
+    const float w = vol.w;
+    const double Ld = (double)vol.L;
+    const int64_t lc = (int64_t)c - vol.cell_base;
+    const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+
+    float4 oi[IPL];
+    bool active[IPL];
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+        const int i = ib + lane + 32 * u;
+        active[u] = i < ie;
+        oi[u] = active[u] ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (MODE == ADJOINT) {
+        if (active[0]) li = a.lam[ib + lane];
+    }
+    Acc<MODE, IPL> A;
+
+    const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
+    for (int64_t g0 = e0; g0 < e1; g0 += 32) {
+        const int ng = (int)min((int64_t)32, e1 - g0);
+        // lane l describes entry g0 + l: its j range and image offset Delta
+        int jb = 0, cnt = 0;
+        float Dx = 0.f, Dy = 0.f, Dz = 0.f;
+        if (lane < ng) {
+            const int cp = a.nbr_cell[g0 + lane];
+            const int sh = a.nbr_shift[g0 + lane];
+            jb = a.cell_start[cp];
+            cnt = a.cell_start[cp + 1] - jb;
+            const int64_t lp = (int64_t)cp - vol.cell_base;
+            const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
+            const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
+            // exact in float64: origins are the float32 products used by the binning
+            Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
+            Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
+            Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+        }
+        int pk = 0, poff = 0, pn = 0;  // producer cursor
+        int ck = 0, coff = 0, cn = 0;  // consumer cursor
+        for (int s = 0; s < STAGES; ++s) {  // prologue: fill the ring
+            if (!next_tile<JT>(ng, cnt, pk, poff, pn)) break;
+            ring.issue(a, lane, __shfl_sync(FULL, jb, pk) + poff, pn);
+            poff += pn;
+        }
+        int cur = -1;
+        float op[IPL][3];
+        while (ring.consumed < ring.issued) {
+            next_tile<JT>(ng, cnt, ck, coff, cn);
+            if (!ring.wait_next()) return false;
+            if (ck != cur) {
+                cur = ck;
+                const float dx = __shfl_sync(FULL, Dx, ck), dy = __shfl_sync(FULL, Dy, ck),
+                            dz = __shfl_sync(FULL, Dz, ck);
+#pragma unroll
+                for (int u = 0; u < IPL; ++u) {
+                    op[u][0] = oi[u].x - dx;
+                    op[u][1] = oi[u].y - dy;
+                    op[u][2] = oi[u].z - dz;
+                }
+            }
+            const float4 *tj = ring.tile(ring.consumed % STAGES);
+            if constexpr (MODE == FORCE)
+                tile_force<IPL>(tj, cn, op, K, A);
+            else
+                tile_adjoint(tj, tj + JT, cn, op[0][0], op[0][1], op[0][2], oi[0].w, li.x, li.y, li.z, K, A);
+            A.fold();
+            coff += cn;
+            ++ring.consumed;
+            __syncwarp();
+            if (next_tile<JT>(ng, cnt, pk, poff, pn)) {
+                ring.issue(a, lane, __shfl_sync(FULL, jb, pk) + poff, pn);
+                poff += pn;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+        if (!active[u]) continue;
+        const int o = a.perm[ib + lane + 32 * u];
+        if constexpr (MODE == FORCE) {
+            a.out_x[o] = A.h[u][0] + A.l[u][0];
+            a.out_y[o] = A.h[u][1] + A.l[u][1];
+            a.out_z[o] = A.h[u][2] + A.l[u][2];
+        } else {
+            const float U0 = A.hu[0] + A.lu[0], U1 = A.hu[1] + A.lu[1], U2 = A.hu[2] + A.lu[2];
+            const float X0 = A.hx[0] + A.lx[0], X1 = A.hx[1] + A.lx[1], X2 = A.hx[2] + A.lx[2];
+            const float Vs = A.hv + A.lv;
+            a.out_x[o] = fmaf(oi[0].w, U0, fmaf(-li.x, Vs, X0));
+            a.out_y[o] = fmaf(oi[0].w, U1, fmaf(-li.y, Vs, X1));
+            a.out_z[o] = fmaf(oi[0].w, U2, fmaf(-li.z, Vs, X2));
+            if (a.out_m) a.out_m[o] = -(A.hg + A.lg);
+        }
+    }
+    return true;
+}
+
+// Persistent work-stealing kernel: each warp takes tasks from a global
+// counter until none is left.  A task of more than 32 particles runs two i
+// particles per lane in the forward pass, and as 32-particle halves in the
+// adjoint.
+template <int MODE, int JT, int STAGES>
+__global__ void __launch_bounds__(256, 3) k_pairs(const KArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int NBUF = MODE == ADJOINT ? 2 : 1;
     constexpr int WARP_BYTES = warp_smem_bytes(MODE, JT, STAGES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + (size_t)warp * WARP_BYTES;
-    float4 *tiles = reinterpret_cast<float4 *>(wbase);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wbase + STAGES * NBUF * JT * 16);
+    Ring<MODE, JT, STAGES> ring;
+    ring.tiles = reinterpret_cast<float4 *>(wbase);
+    ring.bars = reinterpret_cast<uint64_t *>(wbase + STAGES * Ring<MODE, JT, STAGES>::NBUF * JT * 16);
 
     if (lane == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncwarp();
 
-    const PairConsts &K = a.k;
     const int ntask = *a.n_tasks;
-    uint32_t issued = 0, consumed = 0;  // lifetime tile counters of this warp's ring
-
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntask) break;
-        const int4 task = a.tasks[t];
-        const int c = task.x, ib = task.y, ie = task.z;
+        const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
-        const int n = vol.n;
-        const float w = vol.w;
-        const double Ld = (double)vol.L;
-        const int64_t lc = (int64_t)c - vol.cell_base;
-        const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
-
-        const int i = ib + lane;
-        const bool active = i < ie;
-        float4 oi = active ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (MODE == ADJOINT && active) li = a.lam[i];
-        Acc<MODE> A;
-
-        const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
-        bool failed = false;
-        for (int64_t g0 = e0; g0 < e1 && !failed; g0 += 32) {
-            const int ng = (int)min((int64_t)32, e1 - g0);
-            // lane l describes entry g0 + l: its j range and image offset Delta
-            int jb = 0, cnt = 0;
-            float Dx = 0.f, Dy = 0.f, Dz = 0.f;
-            if (lane < ng) {
-                const int cp = a.nbr_cell[g0 + lane];
-                const int sh = a.nbr_shift[g0 + lane];
-                jb = a.cell_start[cp];
-                cnt = a.cell_start[cp + 1] - jb;
-                const int64_t lp = (int64_t)cp - vol.cell_base;
-                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-                const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-                // exact in float64: origins are the float32 products used by the binning
-                Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
-            }
-            int pk = 0, poff = 0, pn = 0;  // producer cursor
-            int ck = 0, coff = 0, cn = 0;  // consumer cursor
-            // prologue: fill the ring
-            for (int s = 0; s < STAGES; ++s) {
-                if (!next_tile<JT>(ng, cnt, pk, poff, pn)) break;
-                const int pjb = __shfl_sync(FULL, jb, pk);
-                if (lane == 0) {
-                    const uint32_t st = issued % STAGES;
-                    tma_issue(smem_addr(&bars[st]), smem_addr(tiles + (size_t)st * NBUF * JT), a.pos + pjb + poff,
-                              pn * 16, smem_addr(tiles + (size_t)st * NBUF * JT + JT),
-                              MODE == ADJOINT ? (const void *)(a.lam + pjb + poff) : nullptr);
-                }
-                poff += pn;
-                ++issued;
-            }
-            int cur = -1;
-            float oxp = 0.f, oyp = 0.f, ozp = 0.f;
-            while (consumed < issued) {
-                next_tile<JT>(ng, cnt, ck, coff, cn);
-                const uint32_t st = consumed % STAGES;
-                if (!warp_wait(smem_addr(&bars[st]), (consumed / STAGES) & 1u)) {
-                    failed = true;
-                    break;
-                }
-                if (ck != cur) {
-                    cur = ck;
-                    oxp = oi.x - __shfl_sync(FULL, Dx, ck);
-                    oyp = oi.y - __shfl_sync(FULL, Dy, ck);
-                    ozp = oi.z - __shfl_sync(FULL, Dz, ck);
-                }
-                const float4 *tj = tiles + (size_t)st * NBUF * JT;
-                if constexpr (MODE == FORCE)
-                    tile_force(tj, cn, oxp, oyp, ozp, K, A);
-                else
-                    tile_adjoint(tj, tj + JT, cn, oxp, oyp, ozp, oi.w, li.x, li.y, li.z, K, A);
-                A.fold();
-                coff += cn;
-                ++consumed;
-                __syncwarp();
-                if (next_tile<JT>(ng, cnt, pk, poff, pn)) {
-                    const int pjb = __shfl_sync(FULL, jb, pk);
-                    if (lane == 0) {
-                        const uint32_t s2 = issued % STAGES;
-                        tma_issue(smem_addr(&bars[s2]), smem_addr(tiles + (size_t)s2 * NBUF * JT),
-                                  a.pos + pjb + poff, pn * 16, smem_addr(tiles + (size_t)s2 * NBUF * JT + JT),
-                                  MODE == ADJOINT ? (const void *)(a.lam + pjb + poff) : nullptr);
-                    }
-                    poff += pn;
-                    ++issued;
-                }
-            }
+        bool ok = true;
+        if constexpr (MODE == FORCE) {
+            if (task.z - task.y > 32)
+                ok = run_task<MODE, JT, STAGES, 2>(a, ring, lane, task.x, task.y, task.z, vol);
+            else
+                ok = run_task<MODE, JT, STAGES, 1>(a, ring, lane, task.x, task.y, task.z, vol);
+        } else {
+            for (int ib = task.y; ib < task.z && ok; ib += 32)
+                ok = run_task<MODE, JT, STAGES, 1>(a, ring, lane, task.x, ib, min(ib + 32, task.z), vol);
         }
-        if (failed) {
+        if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
-            // let the copies still in flight land (bounded) before leaving
-            while (consumed < issued) {
-                const uint32_t st = consumed % STAGES;
-                warp_wait(smem_addr(&bars[st]), (consumed / STAGES) & 1u);
-                ++consumed;
-            }
+            ring.drain();
             return;
-        }
-        if (active) {
-            const int o = a.perm[i];
-            if constexpr (MODE == FORCE) {
-                a.out_x[o] = A.hx + A.lx;
-                a.out_y[o] = A.hy + A.ly;
-                a.out_z[o] = A.hz + A.lz;
-            } else {
-                const Acc<ADJOINT> &J = A;
-                const float U0 = J.hu[0] + J.lu[0], U1 = J.hu[1] + J.lu[1], U2 = J.hu[2] + J.lu[2];
-                const float X0 = J.hx[0] + J.lx[0], X1 = J.hx[1] + J.lx[1], X2 = J.hx[2] + J.lx[2];
-                const float Vs = J.hv + J.lv;
-                a.out_x[o] = fmaf(oi.w, U0, fmaf(-li.x, Vs, X0));
-                a.out_y[o] = fmaf(oi.w, U1, fmaf(-li.y, Vs, X1));
-                a.out_z[o] = fmaf(oi.w, U2, fmaf(-li.z, Vs, X2));
-                if (a.out_m) a.out_m[o] = -(J.hg + J.lg);
-            }
         }
     }
 }
@@ -467,7 +562,7 @@ hacc_launch default_launch(int mode)
 {
     hacc_launch L;
     L.warps_per_cta = 8;
-    L.ctas_per_sm = 2;
+    L.ctas_per_sm = 3;
     L.jtile = mode == FORCE ? 64 : 64;
     L.stages = 4;
     return L;
@@ -483,10 +578,10 @@ int check_common(const hacc_mesh *mesh, const hacc_binned *b, const hacc_lists *
     if (!b->cell_start || !b->perm || !b->sorted4 || !aligned16(b->sorted4)) return HACC_ERR_INVALID;
     if (!l->nbr_off || !l->n_tasks || (mesh->n_entries > 0 && (!l->nbr_cell || !l->nbr_shift)))
         return HACC_ERR_INVALID;
-    if (!l->tasks || !aligned16(l->tasks)) return HACC_ERR_INVALID;
-    if (l->split_T < 1 || l->split_T > 32) return HACC_ERR_INVALID;  // one i particle per lane
+    if (!l->tasks || !aligned16(l->tasks) || !l->task_order) return HACC_ERR_INVALID;
+    if (l->split_T < 1 || l->split_T > 64) return HACC_ERR_INVALID;  // at most two i particles per lane
     if (launch) {
-        if (launch->warps_per_cta < 1 || launch->warps_per_cta > 16 || launch->ctas_per_sm < 1 ||
+        if (launch->warps_per_cta < 1 || launch->warps_per_cta > 8 || launch->ctas_per_sm < 1 ||
             launch->ctas_per_sm > 8)
             return HACC_ERR_INVALID;
     }
@@ -521,6 +616,7 @@ extern "C" int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, c
     a.nbr_cell = lists->nbr_cell;
     a.nbr_shift = lists->nbr_shift;
     a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
+    a.order = lists->task_order;
     a.n_tasks = lists->n_tasks;
     a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
     a.lam = nullptr;
@@ -560,6 +656,7 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     a.nbr_cell = lists->nbr_cell;
     a.nbr_shift = lists->nbr_shift;
     a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
+    a.order = lists->task_order;
     a.n_tasks = lists->n_tasks;
     a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
     a.lam = F.lam;

@@ -116,13 +116,39 @@ __global__ void k_lists_finish(const int32_t *__restrict__ task_off, int64_t n_c
     if (n_pairs) *n_pairs -= N;  // each particle meets itself once in its own cell
 }
 
+// Cost class of each task slot for the heaviest-first order: key =
+// 63 - floor(log2(particles x list length)); empty slots past the task count
+// get 255 and sort last.
+__global__ void __launch_bounds__(256)
+k_task_keys(const int4 *__restrict__ tasks, const int32_t *__restrict__ n_tasks, int64_t cap,
+            const int32_t *__restrict__ cell_start, const int64_t *__restrict__ nbr_off,
+            const int32_t *__restrict__ nbr_cell, int32_t *__restrict__ keys)
+{
+    const int64_t nt = *n_tasks;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cap;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t >= nt) {
+            keys[t] = 255;
+            continue;
+        }
+        const int4 tk = tasks[t];
+        int64_t nj = 0;
+        for (int64_t e = nbr_off[tk.x]; e < nbr_off[tk.x + 1]; ++e) {
+            const int cp = nbr_cell[e];
+            nj += cell_start[cp + 1] - cell_start[cp];
+        }
+        const uint64_t cost = (uint64_t)(tk.z - tk.y) * (uint64_t)(nj > 0 ? nj : 1);
+        keys[t] = 63 - (63 - __clzll((long long)cost));
+    }
+}
+
 struct ListWs {
-    int32_t *nt, *task_off;
-    char *scan_ws;
+    int32_t *nt, *task_off, *keys;
+    char *scan_ws, *sort_ws;
     size_t total;
 };
 
-ListWs lists_layout(const hacc_mesh *mesh, void *ws)
+ListWs lists_layout(const hacc_mesh *mesh, int64_t cap, void *ws)
 {
     ListWs L{};
     char *p = reinterpret_cast<char *>(ws);
@@ -135,6 +161,8 @@ ListWs lists_layout(const hacc_mesh *mesh, void *ws)
     L.nt = reinterpret_cast<int32_t *>(take((size_t)mesh->n_cells * 4));
     L.task_off = reinterpret_cast<int32_t *>(take((size_t)(mesh->n_cells + 1) * 4));
     L.scan_ws = take(scan_workspace_bytes(mesh->n_cells));
+    L.keys = reinterpret_cast<int32_t *>(take((size_t)cap * 4));
+    L.sort_ws = take(sort_workspace_bytes(cap));
     L.total = off;
     return L;
 }
@@ -154,7 +182,8 @@ using namespace hacc;
 
 extern "C" size_t hacc_lists_workspace_size(const hacc_mesh *mesh)
 {
-    return mesh ? lists_layout(mesh, nullptr).total : 0;
+    // sized for the largest task buffer a split of one particle could need
+    return mesh ? lists_layout(mesh, hacc_task_capacity(mesh, 1), nullptr).total : 0;
 }
 
 extern "C" int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
@@ -167,7 +196,8 @@ extern "C" int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned
     if (mesh->n_entries > 0 && (!lists->nbr_cell || !lists->nbr_shift)) return HACC_ERR_INVALID;
     if (lists->task_cap > 0 && !lists->tasks) return HACC_ERR_INVALID;
     if (!aligned16(lists->tasks)) return HACC_ERR_INVALID;
-    ListWs L = lists_layout(mesh, ws);
+    if (lists->task_cap > 0 && !lists->task_order) return HACC_ERR_INVALID;
+    ListWs L = lists_layout(mesh, lists->task_cap, ws);
     if (ws_bytes < L.total) return HACC_ERR_CAPACITY;
     cudaStream_t st = as_stream(stream);
     const int64_t nc = mesh->n_cells;
@@ -191,5 +221,13 @@ extern "C" int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned
     k_lists_finish<<<1, 1, 0, st>>>(L.task_off, nc, lists->task_cap, mesh->N, lists->n_tasks,
                                     lists->n_pairs, status);
     HACC_LAUNCH_CHECK();
+    if (lists->task_cap > 0) {
+        int gt = grid_cells(lists->task_cap);
+        k_task_keys<<<gt, 256, 0, st>>>(reinterpret_cast<const int4 *>(lists->tasks), lists->n_tasks,
+                                        lists->task_cap, binned->cell_start, lists->nbr_off, lists->nbr_cell, L.keys);
+        HACC_LAUNCH_CHECK();
+        rc = sort_index_stable(L.keys, lists->task_cap, 8, lists->task_order, L.sort_ws, st);
+        if (rc) return rc;
+    }
     return HACC_OK;
 }

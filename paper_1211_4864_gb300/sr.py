@@ -176,8 +176,10 @@ class ShortRange:
         self.tasks = torch.empty((max(self.task_cap, 1), 4), dtype=i32, device=dev)
         self.n_tasks = torch.zeros(1, dtype=i32, device=dev)
         self.n_pairs = torch.zeros(1, dtype=i64, device=dev)
+        self.task_order = torch.empty(max(self.task_cap, 1), dtype=i32, device=dev)
         self.lists = hacc_lists(_ptr(self.nbr_off), _ptr(self.nbr_cell), _ptr(self.nbr_shift), _ptr(self.tasks),
-                                _ptr(self.n_tasks), _ptr(self.n_pairs), self.task_cap, self.split_T, 0)
+                                _ptr(self.n_tasks), _ptr(self.n_pairs), _ptr(self.task_order), self.task_cap,
+                                self.split_T, 0)
         ws_bytes = max(lib.hacc_bin_workspace_size(ctypes.byref(self.mesh)),
                        lib.hacc_lists_workspace_size(ctypes.byref(self.mesh)),
                        lib.hacc_force_workspace_size(ctypes.byref(self.mesh)),

@@ -108,6 +108,16 @@ def check_bin_lists(torch, hs, w: Workload, cell_min, rcut, split_T=32):
     exp = np.concatenate(exp_tasks) if exp_tasks else np.zeros((0, 4), np.int64)
     assert np.array_equal(tasks.astype(np.int64), exp)
     assert sr.pair_count() == exp_pairs
+    # the work order is one valid schedule: a permutation, heaviest cost class
+    # first, ties in task order
+    order = sr.task_order.cpu().numpy()[:nt].astype(np.int64)
+    assert np.array_equal(np.sort(order), np.arange(nt))
+    if nt:
+        cnt_all = np.diff(cs.astype(np.int64))
+        nj = np.array([cnt_all[ncell[off[c]:off[c + 1]]].sum() for c in exp[:, 0]], np.int64)
+        cost = (exp[:, 2] - exp[:, 1]) * np.maximum(nj, 1)
+        cls = 63 - np.floor(np.log2(cost.astype(np.float64))).astype(np.int64)
+        assert np.array_equal(order, np.argsort(cls, kind="stable"))
     return sr
 
 
@@ -155,7 +165,7 @@ def test_force_uniform4096_full_oracle(torch, hs):
     assert mx < MAX_TOL, mx
 
 
-@pytest.mark.parametrize("launch", [None, (4, 1, 32, 2), (16, 1, 128, 4), (8, 2, 64, 3), (2, 4, 256, 2)])
+@pytest.mark.parametrize("launch", [None, (4, 1, 32, 2), (8, 1, 128, 4), (8, 2, 64, 3), (2, 4, 256, 2)])
 def test_force_launch_shapes_agree(torch, hs, launch):
     w = uniform_box(3000, 14.0, seed=17)
     prm = params(hs)
@@ -172,7 +182,7 @@ def test_force_clustered_and_fine_mesh(torch, hs):
     w = clustered_box(24, 6, seed=12)
     prm = params(hs)
     ref = oracle_force(w, prm)
-    for cell_min, T in [(3.0, 32), (3.0, 5), (1.5, 32)]:
+    for cell_min, T in [(3.0, 32), (3.0, 5), (3.0, 64), (3.0, 47), (1.5, 64)]:
         _, _, _, a = run_force(torch, hs, w, prm, cell_min=cell_min, split_T=T)
         rms, mx = err_norms(a, ref)
         assert rms < RMS_TOL and mx < MAX_TOL, (cell_min, T, rms, mx)

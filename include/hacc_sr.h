@@ -6,16 +6,16 @@
  * SC'12; arXiv:1211.4864):
  *
  *   a_i = sum_{j != i, s_ij < r_c^2} m_j f_SR(s_ij) d_ij,
- *   f_SR(s) = (s + eps)^(-3/2) - poly[5](s),      s = d.d      (Eq. 4)
+ *   f_SR(s) = (s + eps)^(-3/2) - poly[5](s),      s = d.d      (Eq. 7)
  *
  * where d_ij = x_j - x_i is the minimum periodic image, poly[5] is the
  * fifth-order fit of the filtered grid force (Sec. II), eps the short-distance
  * cutoff (softening, added to s) and r_c the matching radius of the force
  * split (3 grid cells, Sec. II).  The paper evaluates it with an RCB tree and
- * leaf-shared neighbour lists on the BG/Q (Sec. IV); this library bins the
+ * leaf-shared neighbour lists on the BG/Q (Sec. III); this library bins the
  * particles into a periodic chaining mesh (cell width >= the mesh's minimum
  * width), builds per-cell neighbour-cell lists, evaluates the pair force on the
- * GPU, and applies the kick of the split-operator step (Eq. 3).
+ * GPU, and applies the kick of the split-operator step (Eq. 6).
  *
  * Conventions for every call
  * --------------------------
@@ -137,7 +137,7 @@ uint64_t hacc_kernel_launches(void);
  *   rcut         cutoff; requires L >= 2 r_c and n >= 2 R + 1 (unique image)
  *   table[V]     host out: the volumes; copy it to the device for the calls
  *   out_mesh     host out: totals (its `vols` is left NULL for the caller)
- * The chaining mesh stands in for the paper's RCB tree (Sec. IV-A).
+ * The chaining mesh stands in for the paper's RCB tree (Sec. III).
  * Returns HACC_ERR_INVALID on any violated requirement. */
 int hacc_mesh_plan(int32_t V, const float *L, const int64_t *vol_off, float cell_min, float rcut,
                    hacc_volume *table, hacc_mesh *out_mesh);
@@ -146,7 +146,7 @@ int hacc_mesh_plan(int32_t V, const float *L, const int64_t *vol_off, float cell
 size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
 
 /* Bins the particles into the chaining mesh: the analogue of the paper's
- * three-phase structure-of-arrays partition (Sec. IV-A), done as a stable
+ * three-phase structure-of-arrays partition (Sec. III), done as a stable
  * counting sort.  For particle i of volume v, per axis: xw = x - L floor(x/L)
  * (one correction step keeps xw in [0, L)), cell c = min(n-1, floor(xw inv_w)),
  * offset o = xw - c w, each a single float32 round-to-nearest operation.
@@ -165,8 +165,8 @@ size_t hacc_lists_workspace_size(const hacc_mesh *mesh);
 
 /* Builds the per-cell neighbour-cell lists within the cutoff -- the
  * analogue of the paper's tree walk producing leaf-shared interaction lists
- * (Sec. IV-A, walk minimisation; every particle of a cell shares the cell's
- * list, Sec. IV-B) -- and the task list.  A cell c' (with periodic image) is
+ * (Sec. III, walk minimisation; every particle of a cell shares the cell's
+ * list, Sec. III) -- and the task list.  A cell c' (with periodic image) is
  * listed for cell c iff the two boxes can hold a pair closer than r_c:
  * sum_a max(0, |delta_a| - 1)^2 w^2 < r_c^2 (float64), delta = integer cell
  * offset; entries in ascending (dz, dy, dx).  Tasks cut each cell's sorted
@@ -181,9 +181,9 @@ int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hac
 /* Bytes of scratch that hacc_sr_force / hacc_sr_force_adjoint need. */
 size_t hacc_force_workspace_size(const hacc_mesh *mesh);
 
-/* Short-range force (Eq. 4) on every particle, written to ax, ay, az [N] in
+/* Short-range force (Eq. 7) on every particle, written to ax, ay, az [N] in
  * input order (overwritten).  float32 arithmetic with the cutoff applied as a
- * select inside the pair loop (the paper's fsel discussion, Sec. IV-B),
+ * select inside the pair loop (the paper's fsel discussion, Sec. III),
  * rsqrt from the hardware unit, per-particle compensated accumulation.
  * Requires eps > 0 (the softening keeps the self and coincident pairs
  * finite) and p->rcut equal to the rcut the mesh was planned with. */
@@ -204,7 +204,7 @@ int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *binned,
                           float *gm, const hacc_launch *launch, void *ws, size_t ws_bytes,
                           uint32_t *status, void *stream);
 
-/* Kick and optional drift of the split-operator step (Eq. 3):
+/* Kick and optional drift of the split-operator step (Eq. 6):
  *   v <- v + dt_kick a;  then, if x != NULL, x <- x + dt_drift v (new v),
  * the drift computed in float64 and rounded once to float32.  If `mesh` is
  * non-NULL the drifted positions are wrapped into [0, L) of their volume.

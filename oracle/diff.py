@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE (see the package docstring).
 
 Trajectory: ``steps`` repetitions of the short-range kick followed by a drift
-(the kick and stream maps of the paper's split-operator step, Eq. 3):
+(the kick and stream maps of the paper's split-operator step, Eq. 6):
 
     v_{k+1} = v_k + dt a(x_k, m),   x_{k+1} = x_k + dt v_{k+1},
 

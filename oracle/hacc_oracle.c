@@ -10,15 +10,15 @@
  *   a_i = sum_{j != i, s_ij < r_c^2} m_j f_SR(s_ij) d_ij,
  *   f_SR(s) = (s + eps)^(-3/2) - poly(s),  poly(s) = sum_k c_k s^k,
  *
- * (Eq. 4 of the paper, the short-range kernel; s = r.r; the cutoff test is
+ * (Eq. 7 of the paper, the short-range kernel; s = r.r; the cutoff test is
  * folded into the pair loop as in the paper's discussion of the select
- * instruction, Sec. IV-B), with d_ij = x_j - x_i taken as the minimum periodic
+ * instruction, Sec. III), with d_ij = x_j - x_i taken as the minimum periodic
  * image, evaluated in float64 by brute force over all j.  Positions and masses
  * are float64 arrays (float32 inputs widened, or a float64 trajectory).
  *
  * The chaining-mesh binning reference follows the float32 expression sequence
  * that defines a particle's cell (the build's reading of the paper's spatial
- * partition, Sec. IV-A: a mesh replaces the RCB tree): wrap into [0, L), cell
+ * partition, Sec. III: a mesh replaces the RCB tree): wrap into [0, L), cell
  * index per axis, cell-relative offset.  Each step is a single IEEE float32
  * operation with round-to-nearest; this file must be compiled with
  * -ffp-contract=off so that no step is fused.
@@ -203,7 +203,7 @@ int64_t ora_tasks(const int32_t *cell_start, int64_t ncells, int32_t T, int32_t 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Short-range force (Eq. 4), brute force in float64                         */
+/* Short-range force (Eq. 7), brute force in float64                         */
 /* ------------------------------------------------------------------------ */
 
 static double min_image(double d, double L)
@@ -339,7 +339,7 @@ void ora_sr_force_adjoint(const double *x, const double *y, const double *z, con
 }
 
 /* ------------------------------------------------------------------------ */
-/* Kick and drift (the kick/stream maps of Eq. 3's symplectic step)           */
+/* Kick and drift (the kick/stream maps of Eq. 6's symplectic step)           */
 /* ------------------------------------------------------------------------ */
 
 /* v <- v + dt_k a ; then, if x != NULL, x <- x + dt_d v (with the new v),

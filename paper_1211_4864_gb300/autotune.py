@@ -1,7 +1,7 @@
 """Autotuner of the pair-kernel launch shape.
 
 The paper picks its BG/Q operating point (ranks per node x threads per core)
-by measuring the force kernel over neighbour-list sizes (Sec. IV-B, Fig. 5);
+by measuring the force kernel over neighbour-list sizes (Sec. III, Fig. 5);
 the GPU analogue is the launch shape of the persistent pair kernel: warps per
 CTA, resident CTAs per SM, staged j-tile length and pipeline depth.  ``tune``
 times each candidate on the caller's actual mesh and lists with CUDA events

@@ -2,7 +2,7 @@
 // gather of cell-relative float4 (ox, oy, oz, m) into sorted order.
 //
 // The paper's tree build partitions structure-of-arrays particle data in three
-// phases (record, apply to six arrays, apply to the rest; Sec. IV-A) so that
+// phases (record, apply to six arrays, apply to the rest; Sec. III) so that
 // streaming hides memory latency.  The GPU analogue is one streaming pass that
 // computes each particle's cell and its packed (offset, mass) record, a stable
 // radix sort that moves only 8-byte (key, index) pairs, and one gather of the

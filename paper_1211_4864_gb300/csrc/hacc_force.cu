@@ -1,4 +1,4 @@
-// Short-range pair force (Eq. 4 of the paper) and its adjoint.
+// Short-range pair force (Eq. 7 of the paper) and its adjoint.
 //
 // Work decomposition.  A task is a chunk of at most split_T particles of one
 // mesh cell (the "i" particles); one warp owns one task at a time, one i per
@@ -11,7 +11,7 @@
 // clustered particles balance themselves.
 //
 // Arithmetic per pair (float32, cutoff as a select, as in the paper's
-// branch-free kernel, Sec. IV-B):
+// branch-free kernel, Sec. III):
 //   d  = o_j - (o_i - Delta)            cell-relative offsets, Delta = image origin difference
 //   se = eps + d.d                      (three fma)
 //   t  = rsqrt(se)
@@ -200,7 +200,7 @@ __device__ __forceinline__ float rsqrt_hw(float x)
 
 // One pair of the forward law, accumulated into acc[3].  The cutoff test is
 // a compare whose predicate guards the three accumulating fma (no branch, no
-// select): the paper folds the same test into the loop with fsel (Sec. IV-B).
+// select): the paper folds the same test into the loop with fsel (Sec. III).
 __device__ __forceinline__ void pair_force(const float4 p, float oxp, float oyp, float ozp, const PairConsts &K,
                                            float *acc)
 {

@@ -1,4 +1,4 @@
-// Kick / drift maps of the split-operator step (Eq. 3 of the paper) and the
+// Kick / drift maps of the split-operator step (Eq. 6 of the paper) and the
 // float64 global reductions (momentum, Newton-III residual, kinetic energy).
 #include "hacc_common.cuh"
 

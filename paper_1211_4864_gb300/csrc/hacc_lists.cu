@@ -1,7 +1,7 @@
 // Per-cell neighbour-cell lists, task list and candidate-pair count.
 //
 // The paper's RCB tree walk builds one interaction list per leaf that every
-// particle of the leaf shares (walk minimisation, Sec. IV-A/B).  Here a cell
+// particle of the leaf shares (walk minimisation, Sec. III).  Here a cell
 // of the chaining mesh plays the leaf: its list holds the neighbour cells
 // (with their periodic image) whose boxes come closer than r_c.
 #include "hacc_common.cuh"

@@ -3,7 +3,7 @@
 This package is shared by the CUDA path's tests and benchmark and by the CPU
 oracle's tests.  It holds only input generation: particle sets with the
 shapes, sizes and clustering of the paper's workloads, and the default
-coefficients of the grid-force polynomial (an input of the force law, Eq. 4
+coefficients of the grid-force polynomial (an input of the force law, Eq. 7
 of the paper: the paper fits the filtered grid force but does not print the
 fit).  None of the force, binning or list arithmetic lives here.
 """

@@ -1,6 +1,6 @@
 """Default coefficients of the grid-force polynomial f_grid(s) = poly[5](s).
 
-The paper (Sec. II, force-split discussion, and Eq. 4) obtains the filtered
+The paper (Sec. II, force-split discussion, and Eq. 7) obtains the filtered
 grid force numerically, fits it with the right small- and large-distance
 asymptotics, and replaces the fit by a fifth-order polynomial in s = r.r over
 the short-range region.  It prints neither the fit nor the coefficients.  The
@@ -12,7 +12,7 @@ short-range path; this module supplies a physically motivated default:
   It is finite at r = 0 (value 4/(3 sqrt(pi) se^3)) and tends to r^-3 at
   large r, the asymptotics the paper asks of its fit.
 * se^2 = sigma^2 + (n_s + 4) Delta^2 / 6 matches the second moment of the
-  paper's spectral filter exp(-k^2 sigma^2/4) sinc^n_s(k Delta/2) (Eq. 1,
+  paper's spectral filter exp(-k^2 sigma^2/4) sinc^n_s(k Delta/2) (Eq. 5,
   with sigma = 0.8, n_s = 3) times the CIC deposit and interpolation windows
   (two sinc^2 factors per axis), Delta = 1 grid unit.
 * poly is the float64 least-squares fit of degree 5 in s to g on Chebyshev

@@ -1,13 +1,13 @@
 """Seeded particle sets standing in for the paper's cosmology workloads.
 
 The paper runs on cosmological initial conditions and evolved density fields
-(Sec. VI) that are not available here.  These generators produce synthetic
+(Sec. V) that are not available here.  These generators produce synthetic
 sets with the same structure: a near-uniform density of one particle per grid
 cell cubed (the paper's particle loading), optionally perturbed lattices
 (Zel'dovich-style displacement of a lattice, as in cosmological initial
 conditions), and NFW-profile halos that give the very uneven neighbour counts
-of a clustered late-time field (Sec. III notes the short-range solver must
-handle strong clustering).
+of a clustered late-time field (Sec. II: the particle methods handle the
+shortest scales, where clustering is strongest).
 
 All random numbers come from numpy's PCG64 ``default_rng(seed)``, generated in
 float64 and stored as float32, in the order written in each function.
@@ -62,7 +62,7 @@ def _wrap32(pos64: np.ndarray, L32: np.float32) -> np.ndarray:
     return p
 
 
-def _single(name, pos, L32, rng_v=None, **kw) -> Workload:
+def _single(name, pos, L32, **kw) -> Workload:
     n = pos.shape[0]
     x = _wrap32(pos[:, 0], L32)
     y = _wrap32(pos[:, 1], L32)

@@ -157,6 +157,28 @@ int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float 
              const float *m, const hacc_binned *out, void *ws, size_t ws_bytes,
              uint32_t *status, void *stream);
 
+/* Same as hacc_bin, for callers that cannot allocate device memory: a plugin
+ * whose host application owns every device allocation through its own pool,
+ * or code running where cudaMalloc is not allowed or would stall the device
+ * (inside a captured stream, a host callback, a real-time loop).  The scratch
+ * space that hacc_bin takes as `ws` is instead one fixed array that the
+ * library places in device memory when it is loaded: HACC_BIN_NOALLOC_BYTES
+ * (9 MiB), enough for up to 262,144 particles in up to 65,536 cells; every
+ * device that loads the library keeps it until the process exits.  Larger
+ * problems return HACC_ERR_CAPACITY (use hacc_bin with a workspace).  The
+ * caller still passes the inputs and the outputs in `out`; nothing is
+ * allocated or freed, by this library or any other.
+ * The first call on each device looks up the array's device address, with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (on
+ * different streams, or from several host threads) race and must be
+ * serialised by the caller.  Each call clears the scratch it relies on, so
+ * one call's leftovers never change the next call's result.
+ * The paper has no counterpart: this is an interface for embedding. */
+#define HACC_BIN_NOALLOC_BYTES ((size_t)9 << 20)
+int hacc_bin_noalloc(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
+                     const float *m, const hacc_binned *out, uint32_t *status, void *stream);
+
 /* Upper bound of the task count for split size T (host). */
 int64_t hacc_task_capacity(const hacc_mesh *mesh, int32_t split_T);
 

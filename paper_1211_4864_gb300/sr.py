@@ -100,6 +100,13 @@ def hacc_bin(mesh, x, y, z, m, binned, ws, status):
                                _ptr(ws), ws.numel(), _ptr(status), _stream()), "hacc_bin")
 
 
+def hacc_bin_noalloc(mesh, x, y, z, m, binned, status):
+    """hacc_bin without a workspace: the library's fixed device scratch array
+    stands in for it (for callers that cannot allocate device memory)."""
+    check(_lib.load().hacc_bin_noalloc(ctypes.byref(mesh), _ptr(x), _ptr(y), _ptr(z), _ptr(m),
+                                       ctypes.byref(binned), _ptr(status), _stream()), "hacc_bin_noalloc")
+
+
 def hacc_build_lists(mesh, binned, lists, ws, status):
     check(_lib.load().hacc_build_lists(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists), _ptr(ws),
                                        ws.numel(), _ptr(status), _stream()), "hacc_build_lists")

@@ -32,6 +32,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
+# DRAM bytes of one force launch on clustered256, from ncu (profiles/force_clustered256_dram.md),
+# valid only for the kernel source it was measured on
+FORCE_TRAFFIC = {"workload": "clustered256", "bytes": 2132558592 + 954117632,
+                 "source_sha256": "c10a1a0018f88a2f579e8004dd36adb58b449d23ba327fd76397791cfe2c3994"}
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
 WORKLOADS = {
@@ -57,6 +61,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle error check")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="oracle target particles in the CPU baseline")
+    ap.add_argument("--graph", choices=["auto", "on", "off"], default="auto",
+                    help="replay the step as one captured CUDA graph (auto: on for batched256)")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     return ap.parse_args()
 
 
@@ -188,13 +195,14 @@ def run_ours(args):
     v0 = torch.tensor(np.stack([w.vx, w.vy, w.vz]), device=dev)
     v = v0.clone()
     a = torch.empty_like(v)
-    mom = None
     stream = torch.cuda.current_stream()
     f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
+    mom = torch.empty(8, dtype=torch.float64, device=dev)
+    use_graph = args.graph == "on" or (args.graph == "auto" and args.config == "batched256")
+
     def step(k=None):
-        nonlocal mom
         sr.prepare(pos, m)
         if k is not None:
             f0[k].record(stream)
@@ -202,13 +210,27 @@ def run_ours(args):
         if k is not None:
             f1[k].record(stream)
         sr.kick(v, a, w.dt)
-        mom = sr.moments(m, v, a)
+        mom.copy_(sr.moments(m, v, a))
 
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
     sr.check_status()
     pairs = sr.pair_count()
+    graph = None
+    if use_graph:
+        # one captured replay of the whole step; force timing from a separate eager pass
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                step()
+        stream.wait_stream(side)
+        for _ in range(max(args.warmup, 1)):
+            graph.replay()
+        torch.cuda.synchronize()
+        sr.check_status()
 
     clocks = ClockSampler(ranks.local)
     clocks.start()
@@ -220,7 +242,10 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        step(k)
+        if graph is not None:
+            graph.replay()
+        else:
+            step(k)
     e1.record(stream)
     torch.cuda.synchronize()
     ranks.barrier()
@@ -229,6 +254,13 @@ def run_ours(args):
     sr.check_status()
     t_ms = e0.elapsed_time(e1)
     t_ms_max = ranks.max(t_ms)
+    if graph is not None:
+        # the replay launches what the capture recorded: count one eager step's kernels
+        l0 = hs.hacc_kernel_launches()
+        for k in range(args.steps):
+            step(k)
+        torch.cuda.synchronize()
+        launches = (hs.hacc_kernel_launches() - l0)
     t_force = statistics.mean(f0[k].elapsed_time(f1[k]) for k in range(args.steps))
     total_pairs = ranks.sum(float(pairs)) * args.steps
     value = total_pairs / (t_ms_max * 1e-3)
@@ -238,9 +270,10 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "N": w.N, "volumes": w.V,
                       "pairs_per_step": pairs, "replicas": ranks.world,
-                      "l2": "inputs larger than L2 (sorted float4 268 MB + SoA positions 201 MB for "
-                            "clustered256); no flush between steps",
+                      "l2": f"inputs larger than L2 (sorted float4 {16 * w.N / 1e6:.0f} MB + SoA positions "
+                            f"{12 * w.N / 1e6:.0f} MB vs 126 MB L2); no flush between steps",
                       "launch": launch.__dict__ if launch else "default", "split_T": split_T,
+                      "cuda_graph": graph is not None,
                       "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
            "gpu_launches": int(launches), "clocks": clk}
 
@@ -256,7 +289,8 @@ def run_ours(args):
     peak = sms * 128 * 2 * f_max * 1e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
     out["roofline"] = {"bound": "alu", "kernel": "k_pairs<FORCE> (hacc_sr_force)", "achieved": achieved,
-                       "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                       "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                       "traffic": force_traffic(args.config),
                        "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (max SM clock)",
                        "flops_per_pair": FLOPS_PER_PAIR, "force_ms": t_force,
                        "force_share": t_force / (t_ms / args.steps)}
@@ -278,6 +312,10 @@ def run_ours(args):
     out["fwd_adjoint"] = {"force_ms": t_force, "adjoint_ms": t_adj, "ratio_fwd_plus_adj_over_fwd":
                           (t_force + t_adj) / t_force}
 
+    # differentiation workload: forward trajectory vs forward + backward
+    if not args.no_diff and ranks.rank == 0:
+        out["differentiation"] = differentiation(torch, hs)
+
     # end to end through the public API with host buffers
     if not args.no_e2e:
         out["e2e"] = e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs)
@@ -291,6 +329,64 @@ def run_ours(args):
     if ranks.rank == 0:
         print(json.dumps(out), flush=True)
     ranks.close()
+
+
+def differentiation(torch, hs, reps: int = 3):
+    """diff64 workload (64^3 clustered particles, 100 halos, L = 64): four
+    kick-drift steps and the weighted squared-displacement loss, forward only
+    vs forward + backward through the hand-written adjoint."""
+    from synth import default_coeffs, make_config
+    w = make_config("diff64")
+    prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
+    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=64)
+    x0 = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda", requires_grad=True)
+    v0 = torch.zeros_like(x0, requires_grad=True)
+    m = torch.tensor(w.m, device="cuda", requires_grad=True)
+    wt = torch.tensor(w.extra["loss_w"].T.copy(), device="cuda")
+    steps = int(w.extra["steps"])
+
+    def fwd():
+        with torch.no_grad():
+            d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps)
+            return (wt * d * d).sum()
+
+    def fwd_bwd():
+        x0.grad = v0.grad = m.grad = None
+        d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps)
+        loss = (wt * d * d).sum()
+        loss.backward()
+        return loss
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_f = timed(fwd)
+    t_fb = timed(fwd_bwd)
+    sr.check_status()
+    return {"workload": "diff64: 64^3 = 262,144 particles, L = 64, 60% uniform + 40% in 100 NFW halos "
+                        "(seed 4), 4 kick-drift steps of dt = 0.01, loss sum w (x_4 - x_0)^2",
+            "forward_ms": t_f, "forward_backward_ms": t_fb, "ratio_fwd_bwd_over_fwd": t_fb / t_f}
+
+
+def force_traffic(config: str):
+    """Recorded ncu DRAM bytes per force launch, or None if the kernel source changed since."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1211_4864_gb300", "csrc", "hacc_force.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if config != FORCE_TRAFFIC["workload"] or sha != FORCE_TRAFFIC["source_sha256"]:
+        return None
+    return FORCE_TRAFFIC["bytes"]
 
 
 def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
@@ -353,18 +449,24 @@ def check_sample(sr, pos, m, prm, w, launch, S=256):
 
 
 def cpu_baseline(w, prm, S):
-    """The float64 oracle on a bounded sample of the same workload (all host cores)."""
+    """The float64 oracle on a bounded sample of the same workload (all host cores);
+    for several volumes, the most populated one."""
     import oracle
+    v = int(np.argmax(np.diff(w.vol_off)))
+    b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+    n = e - b
     rng = np.random.default_rng(12)
-    tg = rng.choice(w.N, size=min(S, w.N), replace=False)
-    x, y, z, m = (np.ascontiguousarray(q, dtype=np.float64) for q in (w.x, w.y, w.z, w.m))
+    # about 6e10 pair evaluations (10-20 s on the box's cores), never below S targets
+    S = min(n, max(S, int(6e10 / max(n, 1))))
+    tg = rng.choice(n, size=S, replace=False)
+    x, y, z, m = (np.ascontiguousarray(q[b:e], dtype=np.float64) for q in (w.x, w.y, w.z, w.m))
     t = time.perf_counter()
-    oracle.sr_force(x, y, z, m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    oracle.sr_force(x, y, z, m, float(w.L[v]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
     dt = time.perf_counter() - t
-    evals = len(tg) * (w.N - 1)
+    evals = len(tg) * (n - 1)
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{len(tg)} seeded target particles x all {w.N - 1} sources (brute force, float64), "
-                      f"{dt:.1f} s"}
+            "sample": f"{len(tg)} seeded target particles x all {n - 1} sources of volume {v} "
+                      f"(brute force, float64), {dt:.1f} s"}
 
 
 # ---------------------------------------------------------------------------

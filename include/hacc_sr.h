@@ -150,14 +150,21 @@ size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
  * counting sort.  For particle i of volume v, per axis: xw = x - L floor(x/L)
  * (one correction step keeps xw in [0, L)), cell c = min(n-1, floor(xw inv_w)),
  * offset o = xw - c w, each a single float32 round-to-nearest operation.
+ * Optional displacements dx, dy, dz (all three or none, [N]): the position is
+ * then x + d, formed, wrapped and offset in float64 (same steps, each one
+ * float64 round-to-nearest operation, the cell from floor(xw inv_w) in
+ * float64) and only the offset o = xw - fl32(c w) is rounded to float32; a
+ * trajectory kept as a fixed reference plus a small drift displacement so
+ * keeps its float64 position to float32 precision of a cell-relative offset.
  * Within a cell the sorted order is ascending input index (bit-exact and
  * deterministic).  x, y, z, m: [N] input order.  Writes every array of `out`.
  * A non-finite coordinate sets HACC_STATUS_NONFINITE and is binned as 0. */
 int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
-             const float *m, const hacc_binned *out, void *ws, size_t ws_bytes,
-             uint32_t *status, void *stream);
+             const float *dx, const float *dy, const float *dz, const float *m,
+             const hacc_binned *out, void *ws, size_t ws_bytes, uint32_t *status, void *stream);
 
-/* Same as hacc_bin, for callers that cannot allocate device memory: a plugin
+/* Same as hacc_bin (absolute positions, no displacements), for callers that
+ * cannot allocate device memory: a plugin
  * whose host application owns every device allocation through its own pool,
  * or code running where cudaMalloc is not allowed or would stall the device
  * (inside a captured stream, a host callback, a real-time loop).  The scratch

@@ -52,9 +52,9 @@ def lib():
             L.ora_num_threads.restype = ctypes.c_int
             L.ora_mesh.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
-            L.ora_bin.argtypes = [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_float,
-                                  ctypes.c_int32, ctypes.c_float, ctypes.c_float,
-                                  _i32p, _i32p, _i32p, _f32p]
+            L.ora_bin.argtypes = [_f32p, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  _f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, ctypes.c_float,
+                                  ctypes.c_float, _i32p, _i32p, _i32p, _f32p]
             L.ora_bin.restype = ctypes.c_int
             L.ora_reach.argtypes = [ctypes.c_float, ctypes.c_float]
             L.ora_reach.restype = ctypes.c_int32
@@ -108,16 +108,22 @@ def mesh(L: float, cell_min: float) -> tuple[int, np.float32, np.float32]:
     return int(n.value), np.float32(w.value), np.float32(iw.value)
 
 
-def bin_volume(x, y, z, m, L: float, cell_min: float) -> dict:
-    """Reference binning of one periodic volume (see ora_bin)."""
+def bin_volume(x, y, z, m, L: float, cell_min: float, disp=None) -> dict:
+    """Reference binning of one periodic volume (see ora_bin); disp: optional
+    float32 displacements [3, N] (the position is then x + d)."""
     n, w, iw = mesh(L, cell_min)
     N = int(np.asarray(x).shape[0])
     cell_of = np.zeros(N, np.int32)
     cell_start = np.zeros(n ** 3 + 1, np.int32)
     perm = np.zeros(N, np.int32)
     sorted4 = np.zeros((N, 4), np.float32)
-    rc = lib().ora_bin(_c32(x), _c32(y), _c32(z), _c32(m), N, float(L), n, float(w), float(iw),
-                       cell_of, cell_start, perm, sorted4.reshape(-1))
+    if disp is None:
+        dptr = (None, None, None)
+    else:
+        d = [_c32(disp[k]) for k in range(3)]
+        dptr = tuple(a.ctypes.data for a in d)
+    rc = lib().ora_bin(_c32(x), _c32(y), _c32(z), dptr[0], dptr[1], dptr[2], _c32(m), N, float(L), n,
+                       float(w), float(iw), cell_of, cell_start, perm, sorted4.reshape(-1))
     assert rc == 0
     return dict(n=n, w=w, inv_w=iw, cell_of=cell_of, cell_start=cell_start, perm=perm,
                 sorted4=sorted4)

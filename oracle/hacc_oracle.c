@@ -69,6 +69,47 @@ static float wrap32(float x, float L)
     return xw;
 }
 
+static int32_t cell1(float xw, float inv_w, int32_t n);
+
+/* The same wrap of a float64 position x + d (displacement mode). */
+static double wrap64(double p, double L)
+{
+    double q = floor(p / L);
+    double ql = q * L;
+    double pw = p - ql;
+    if (pw < 0.0) pw = pw + L;
+    if (pw >= L) pw = pw - L;
+    return pw;
+}
+
+static int32_t cell64(double pw, float inv_w, int32_t n)
+{
+    double t = pw * (double)inv_w;
+    int32_t c = (int32_t)floor(t);
+    if (c > n - 1) c = n - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+/* Cell coordinate and cell-relative offset of one coordinate: float32 steps
+ * for an absolute position; with a displacement d (non-NULL), the position
+ * x + d is formed and wrapped in float64 and only the offset is rounded. */
+static int32_t axis_cell(float x, const float *d, int64_t i, float L, int32_t n, float w, float inv_w,
+                         float *o)
+{
+    if (!d) {
+        float xw = wrap32(x, L);
+        int32_t c = cell1(xw, inv_w, n);
+        *o = xw - (float)c * w;
+        return c;
+    }
+    double pw = wrap64((double)x + (double)d[i], (double)L);
+    int32_t c = cell64(pw, inv_w, n);
+    float cw = (float)c * w;
+    *o = (float)(pw - (double)cw);
+    return c;
+}
+
 static int32_t cell1(float xw, float inv_w, int32_t n)
 {
     float t = xw * inv_w;
@@ -81,19 +122,25 @@ static int32_t cell1(float xw, float inv_w, int32_t n)
 /* Binning of one volume.  Outputs: cell_of[i] (cell of particle i), counts per
  * cell, and the stable order: perm[k] = original index of the particle in
  * sorted slot k, particles ordered by cell and, within a cell, by original
- * index.  sorted4[4k..4k+3] = (ox, oy, oz, m) with o = xw - c w (float32).
- * cell_start has n^3 + 1 entries.  Returns 0. */
-int ora_bin(const float *x, const float *y, const float *z, const float *m, int64_t N,
-            float L, int32_t n, float w, float inv_w,
+ * index.  sorted4[4k..4k+3] = (ox, oy, oz, m) with o the cell-relative offset
+ * (float32).  dx, dy, dz: optional displacements (all NULL for absolute
+ * positions).  cell_start has n^3 + 1 entries.  Returns 0. */
+int ora_bin(const float *x, const float *y, const float *z, const float *dx, const float *dy,
+            const float *dz, const float *m, int64_t N, float L, int32_t n, float w, float inv_w,
             int32_t *cell_of, int32_t *cell_start, int32_t *perm, float *sorted4)
 {
     int64_t nc = (int64_t)n * n * n;
     int64_t *cnt = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
-    if (!cnt) return -1;
+    float *off = (float *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(float));
+    if (!cnt || !off) {
+        free(cnt);
+        free(off);
+        return -1;
+    }
     for (int64_t i = 0; i < N; ++i) {
-        int32_t cx = cell1(wrap32(x[i], L), inv_w, n);
-        int32_t cy = cell1(wrap32(y[i], L), inv_w, n);
-        int32_t cz = cell1(wrap32(z[i], L), inv_w, n);
+        int32_t cx = axis_cell(x[i], dx, i, L, n, w, inv_w, &off[3 * i + 0]);
+        int32_t cy = axis_cell(y[i], dy, i, L, n, w, inv_w, &off[3 * i + 1]);
+        int32_t cz = axis_cell(z[i], dz, i, L, n, w, inv_w, &off[3 * i + 2]);
         int32_t c = (cz * n + cy) * n + cx;
         cell_of[i] = c;
         cnt[c] += 1;
@@ -107,20 +154,15 @@ int ora_bin(const float *x, const float *y, const float *z, const float *m, int6
     cell_start[nc] = (int32_t)run;
     /* visiting particles in index order makes the placement stable */
     for (int64_t i = 0; i < N; ++i) {
-        int32_t c = cell_of[i];
-        int64_t k = cnt[c]++;
+        int64_t k = cnt[cell_of[i]]++;
         perm[k] = (int32_t)i;
-        float xw = wrap32(x[i], L), yw = wrap32(y[i], L), zw = wrap32(z[i], L);
-        int32_t cx = c % n, cy = (c / n) % n, cz = c / (n * n);
-        float ox = xw - (float)cx * w;
-        float oy = yw - (float)cy * w;
-        float oz = zw - (float)cz * w;
-        sorted4[4 * k + 0] = ox;
-        sorted4[4 * k + 1] = oy;
-        sorted4[4 * k + 2] = oz;
+        sorted4[4 * k + 0] = off[3 * i + 0];
+        sorted4[4 * k + 1] = off[3 * i + 1];
+        sorted4[4 * k + 2] = off[3 * i + 2];
         sorted4[4 * k + 3] = m[i];
     }
     free(cnt);
+    free(off);
     return 0;
 }
 

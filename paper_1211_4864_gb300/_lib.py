@@ -73,7 +73,8 @@ SIGNATURES = {
     "hacc_mesh_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_float, ctypes.c_float,
                                       _PS(hacc_volume), _PS(hacc_mesh)]),
     "hacc_bin_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh)]),
-    "hacc_bin": (ctypes.c_int, [_PS(hacc_mesh), _P, _P, _P, _P, _PS(hacc_binned), _P, ctypes.c_size_t, _P, _P]),
+    "hacc_bin": (ctypes.c_int, [_PS(hacc_mesh), _P, _P, _P, _P, _P, _P, _P, _PS(hacc_binned), _P, ctypes.c_size_t,
+                                _P, _P]),
     "hacc_bin_noalloc": (ctypes.c_int, [_PS(hacc_mesh), _P, _P, _P, _P, _PS(hacc_binned), _P, _P]),
     "hacc_task_capacity": (ctypes.c_int64, [_PS(hacc_mesh), ctypes.c_int32]),
     "hacc_lists_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh)]),

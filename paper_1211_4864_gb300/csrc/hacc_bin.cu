@@ -29,11 +29,50 @@ __device__ __forceinline__ float sanitize(float v, uint32_t *status)
     return v;
 }
 
+// Position x + d wrapped into [0, L) in float64, each step one
+// round-to-nearest operation (used when displacements are given).
+__device__ __forceinline__ double wrap64(double p, double L)
+{
+    double q = floor(__ddiv_rn(p, L));
+    double pw = __dsub_rn(p, __dmul_rn(q, L));
+    if (pw < 0.0) pw = __dadd_rn(pw, L);
+    if (pw >= L) pw = __dsub_rn(pw, L);
+    return pw;
+}
+
+__device__ __forceinline__ int cell64(double pw, float inv_w, int n)
+{
+    int c = (int)floor(__dmul_rn(pw, (double)inv_w));
+    c = c > n - 1 ? n - 1 : c;
+    return c < 0 ? 0 : c;
+}
+
+// One axis: cell coordinate and cell-relative offset.  Without a
+// displacement every step is float32; with one, the position x + d is formed
+// and wrapped in float64 and only the final offset is rounded to float32.
+__device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, const hacc_volume &vol, float &o,
+                                         uint32_t *status)
+{
+    const float L = vol.L, w = vol.w, iw = vol.inv_w;
+    const int n = vol.n;
+    if (!d) {
+        const float xw = wrap32(sanitize(x, status), L);
+        const int c = cell1(xw, iw, n);
+        o = __fsub_rn(xw, __fmul_rn((float)c, w));
+        return c;
+    }
+    const double pw = wrap64(__dadd_rn((double)sanitize(x, status), (double)sanitize(d[i], status)), (double)L);
+    const int c = cell64(pw, iw, n);
+    o = __double2float_rn(__dsub_rn(pw, (double)__fmul_rn((float)c, w)));
+    return c;
+}
+
 // Pass 1: per particle, its cell key, its (offset, mass) record in input
 // order, and the cell histogram.
 __global__ void __launch_bounds__(KEY_THREADS)
 k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *__restrict__ x,
-           const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ m,
+           const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dx,
+           const float *__restrict__ dy, const float *__restrict__ dz, const float *__restrict__ m,
            int32_t *__restrict__ cell_of, int32_t *__restrict__ keys, float4 *__restrict__ rec,
            int32_t *__restrict__ counts, uint32_t *status)
 {
@@ -41,19 +80,14 @@ k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *
          i += (int64_t)gridDim.x * blockDim.x) {
         int v = find_volume_by_particle(vols, V, i);
         const hacc_volume &vol = vols[v];
-        float L = vol.L, w = vol.w, iw = vol.inv_w;
-        int n = vol.n;
-        float xw = wrap32(sanitize(x[i], status), L);
-        float yw = wrap32(sanitize(y[i], status), L);
-        float zw = wrap32(sanitize(z[i], status), L);
-        int cx = cell1(xw, iw, n), cy = cell1(yw, iw, n), cz = cell1(zw, iw, n);
+        const int n = vol.n;
+        float4 r;
+        const int cx = axis_cell(x[i], dx, i, vol, r.x, status);
+        const int cy = axis_cell(y[i], dy, i, vol, r.y, status);
+        const int cz = axis_cell(z[i], dz, i, vol, r.z, status);
         int32_t key = (int32_t)(vol.cell_base + ((int64_t)cz * n + cy) * n + cx);
         cell_of[i] = key;
         keys[i] = key;
-        float4 r;
-        r.x = __fsub_rn(xw, __fmul_rn((float)cx, w));
-        r.y = __fsub_rn(yw, __fmul_rn((float)cy, w));
-        r.z = __fsub_rn(zw, __fmul_rn((float)cz, w));
         r.w = m[i];
         rec[i] = r;
         atomicAdd(&counts[key], 1);
@@ -238,9 +272,10 @@ extern "C" size_t hacc_bin_workspace_size(const hacc_mesh *mesh)
 }
 
 extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
-                        const float *m, const hacc_binned *out, void *ws, size_t ws_bytes,
-                        uint32_t *status, void *stream)
+                        const float *dx, const float *dy, const float *dz, const float *m,
+                        const hacc_binned *out, void *ws, size_t ws_bytes, uint32_t *status, void *stream)
 {
+    if ((dx || dy || dz) && !(dx && dy && dz)) return HACC_ERR_INVALID;
     if (!mesh || !out || !mesh->vols || mesh->V < 1 || mesh->N < 0 || !status) return HACC_ERR_INVALID;
     if (!out->cell_start || !ws || !aligned16(ws)) return HACC_ERR_INVALID;
     const int64_t N = mesh->N;
@@ -254,7 +289,7 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     HACC_CUDA_TRY(cudaMemsetAsync(b.counts, 0, (size_t)mesh->n_cells * 4, st));
     if (N > 0) {
         k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(
-            mesh->vols, mesh->V, N, x, y, z, m, out->cell_of, b.keys, b.rec, b.counts, status);
+            mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m, out->cell_of, b.keys, b.rec, b.counts, status);
         HACC_LAUNCH_CHECK();
     }
     int rc = scan_exclusive_i32(b.counts, out->cell_start, mesh->n_cells, b.scan_ws, st);

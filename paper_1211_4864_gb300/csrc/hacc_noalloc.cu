@@ -52,5 +52,5 @@ extern "C" int hacc_bin_noalloc(const hacc_mesh *mesh, const float *x, const flo
     // hacc_bin clears the cell counts it accumulates and overwrites every
     // other scratch word before reading it, so the previous call's contents
     // never leak into this one.
-    return hacc_bin(mesh, x, y, z, m, out, ws, NOALLOC_BIN_BYTES, status, stream);
+    return hacc_bin(mesh, x, y, z, nullptr, nullptr, nullptr, m, out, ws, NOALLOC_BIN_BYTES, status, stream);
 }

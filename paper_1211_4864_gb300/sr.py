@@ -95,9 +95,9 @@ def hacc_mesh_plan(L, vol_off, cell_min: float, rcut: float):
     return table, mesh
 
 
-def hacc_bin(mesh, x, y, z, m, binned, ws, status):
-    check(_lib.load().hacc_bin(ctypes.byref(mesh), _ptr(x), _ptr(y), _ptr(z), _ptr(m), ctypes.byref(binned),
-                               _ptr(ws), ws.numel(), _ptr(status), _stream()), "hacc_bin")
+def hacc_bin(mesh, x, y, z, m, binned, ws, status, dx=None, dy=None, dz=None):
+    check(_lib.load().hacc_bin(ctypes.byref(mesh), _ptr(x), _ptr(y), _ptr(z), _ptr(dx), _ptr(dy), _ptr(dz), _ptr(m),
+                               ctypes.byref(binned), _ptr(ws), ws.numel(), _ptr(status), _stream()), "hacc_bin")
 
 
 def hacc_bin_noalloc(mesh, x, y, z, m, binned, status):
@@ -195,8 +195,11 @@ class ShortRange:
         self.status = torch.zeros(1, dtype=i32, device=dev)
 
     # -- calls ------------------------------------------------------------
-    def bin(self, x, y, z, m):
-        hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status)
+    def bin(self, x, y, z, m, disp=None):
+        if disp is None:
+            hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status)
+        else:
+            hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status, disp[0], disp[1], disp[2])
 
     def build_lists(self):
         hacc_build_lists(self.mesh, self.binned, self.lists, self.ws, self.status)
@@ -236,9 +239,10 @@ class ShortRange:
         hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.ws)
         return out
 
-    def prepare(self, pos, m):
-        """Binning and lists for positions pos [3, N] and masses m [N]."""
-        self.bin(pos[0], pos[1], pos[2], m)
+    def prepare(self, pos, m, disp=None):
+        """Binning and lists for positions pos [3, N] (plus displacements disp
+        [3, N], if given: the position is then pos + disp) and masses m [N]."""
+        self.bin(pos[0], pos[1], pos[2], m, disp)
         self.build_lists()
 
     def check_status(self):
@@ -257,22 +261,23 @@ class ShortRange:
 
 class _SRForce(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, pos, m, solver: ShortRange, params: SRParams):
-        solver.prepare(pos, m)
+    def forward(ctx, pos, disp, m, solver: ShortRange, params: SRParams):
+        solver.prepare(pos, m, disp)
         a = solver.force(params)
-        ctx.save_for_backward(pos, m)
+        ctx.save_for_backward(pos, disp, m)
         ctx.solver = solver
         ctx.params = params
         return a
 
     @staticmethod
     def backward(ctx, ga):
-        pos, m = ctx.saved_tensors
+        pos, disp, m = ctx.saved_tensors
         solver = ctx.solver
         # the pair terms are recomputed: re-bin the saved positions, then the adjoint
-        solver.prepare(pos, m)
-        gpos, gm = solver.adjoint(ctx.params, ga.contiguous(), want_gm=ctx.needs_input_grad[1])
-        return gpos, gm, None, None
+        solver.prepare(pos, m, disp)
+        gpos, gm = solver.adjoint(ctx.params, ga.contiguous(), want_gm=ctx.needs_input_grad[2])
+        # the position is pos + disp: both receive the same cotangent
+        return gpos, gpos if ctx.needs_input_grad[1] else None, gm, None, None
 
 
 class _KickDrift(torch.autograd.Function):
@@ -305,10 +310,28 @@ class _KickDrift(torch.autograd.Function):
         return gv, gp2, ga, None, None
 
 
-def sr_force_autograd(pos, m, solver: ShortRange, params: SRParams):
-    """Accelerations [3, N] of positions pos [3, N]; differentiable in pos and m."""
-    return _SRForce.apply(pos.contiguous(), m.contiguous(), solver, params)
+def sr_force_autograd(pos, m, solver: ShortRange, params: SRParams, disp=None):
+    """Accelerations [3, N] at positions pos [3, N] (+ disp [3, N] if given);
+    differentiable in pos, disp and m."""
+    return _SRForce.apply(pos.contiguous(), None if disp is None else disp.contiguous(), m.contiguous(), solver,
+                          params)
 
 
 def kick_drift_autograd(v, pos, a, dt_k: float, dt_d: float):
+    """(v + dt_k a, pos + dt_d (v + dt_k a)); differentiable."""
     return _KickDrift.apply(v.contiguous(), pos.contiguous(), a.contiguous(), dt_k, dt_d)
+
+
+def trajectory_autograd(x0, v0, m, solver: ShortRange, params: SRParams, dt: float, steps: int):
+    """`steps` short-range kick-drift steps (the kick and stream maps of the
+    paper's split-operator step, Eq. 6) from positions x0 [3, N] and velocities
+    v0 [3, N].  Positions stay x0 + disp with a float32 displacement that the
+    drift updates, so they keep float32 precision of the displacement rather
+    than of the box.  Returns (disp, v) after the last step; differentiable in
+    x0, v0 and m."""
+    disp = torch.zeros_like(x0)
+    v = v0
+    for _ in range(steps):
+        a = sr_force_autograd(x0, m, solver, params, disp)
+        v, disp = kick_drift_autograd(v, disp, a, dt, dt)
+    return disp, v

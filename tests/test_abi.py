@@ -114,7 +114,8 @@ def test_workspace_queries_positive(lib):
 def test_device_calls_reject_bad_arguments_on_host(lib):
     """Argument checks run before any CUDA call (safe without a GPU)."""
     rc, table, mesh = _plan([16.0], [0, 10], 3.0, 3.0)
-    assert lib.hacc_bin(None, None, None, None, None, None, None, 0, None, None) == _lib.HACC_ERR_INVALID
+    assert lib.hacc_bin(None, None, None, None, None, None, None, None, None, None, 0, None,
+                        None) == _lib.HACC_ERR_INVALID
     assert lib.hacc_kick(None, -1, None, None, None, None, None, None, 0.0, None, None, None, 0.0,
                          None) == _lib.HACC_ERR_INVALID
     assert lib.hacc_moments(5, None, None, None, None, None, None, None, None, None, 0,

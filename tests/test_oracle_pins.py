@@ -321,6 +321,39 @@ def test_binning_invariants_and_numpy_restatement():
     assert np.max(np.abs(diff)) < 1e-5
 
 
+def test_binning_with_displacements_keeps_float64_positions():
+    """Displacement mode: the offset plus the cell origin reproduces the float64
+    position x + d (mod L) to float32 precision of the offset (not of L), and
+    the steps restate bit for bit in numpy float64."""
+    rng = np.random.default_rng(32)
+    L = np.float32(64.0)
+    N = 4000
+    x = (rng.random(N) * L).astype(np.float32)
+    y = (rng.random(N) * L).astype(np.float32)
+    z = (rng.random(N) * L).astype(np.float32)
+    d = (rng.normal(size=(3, N)) * 1e-3).astype(np.float32)
+    d[0, :3] = [-x[0] - np.float32(1e-6), np.float32(70.0), np.float32(-64.5)]
+    m = np.ones(N, np.float32)
+    b = oracle.bin_volume(x, y, z, m, float(L), 3.0, disp=d)
+    n, w, iw = b["n"], b["w"], b["inv_w"]
+    s4, perm = b["sorted4"], b["perm"]
+    pos = np.stack([x, y, z]).astype(np.float64) + d.astype(np.float64)
+    for k in range(3):
+        p = pos[k]
+        q = np.floor(p / np.float64(L))
+        pw = p - q * np.float64(L)
+        pw = np.where(pw < 0, pw + np.float64(L), pw)
+        pw = np.where(pw >= np.float64(L), pw - np.float64(L), pw)
+        c = np.clip(np.floor(pw * np.float64(iw)).astype(np.int64), 0, n - 1)
+        cw = (c.astype(np.float32) * w).astype(np.float32)
+        o = (pw - cw.astype(np.float64)).astype(np.float32)
+        assert np.array_equal(s4[:, k].view(np.int32), o[perm].view(np.int32))
+        err = (o.astype(np.float64) + cw - pw)
+        assert np.max(np.abs(err)) <= 4.0 * np.spacing(np.float32(2 * w))
+    cid = b["cell_of"]
+    assert np.all(np.diff(cid[perm]) >= 0)
+
+
 @pytest.mark.parametrize("L,cell_min,rcut", [(16.0, 3.0, 3.0), (10.0, 2.0, 3.0), (9.0, 3.0, 3.0),
                                              (13.0, 1.4, 3.0)])
 def test_lists_cover_every_pair_within_cutoff(L, cell_min, rcut):

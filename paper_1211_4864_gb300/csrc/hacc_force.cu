@@ -31,7 +31,10 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 constexpr uint32_t WAIT_HINT_NS = 100000;  // a waiting warp may sleep up to 0.1 ms per try
 
-enum Mode { FORCE = 0, ADJOINT = 1 };
+// FORCE: accelerations.  ADJOINT: dL/dx.  ADJOINT_GM: dL/dx and dL/dm.
+enum Mode { FORCE = 0, ADJOINT = 1, ADJOINT_GM = 2 };
+
+__host__ __device__ constexpr bool is_adjoint(int mode) { return mode != FORCE; }
 
 struct PairConsts {
     float eps;      // softening
@@ -166,27 +169,48 @@ struct Acc<FORCE, IPL> {
     }
 };
 
-template <int IPL>
-struct Acc<ADJOINT, IPL> {
-    static_assert(IPL == 1, "the adjoint runs one i particle per lane");
-    float u[3] = {0.f, 0.f, 0.f}, x[3] = {0.f, 0.f, 0.f}, v = 0.f, g = 0.f;
-    float hu[3] = {0.f, 0.f, 0.f}, lu[3] = {0.f, 0.f, 0.f};
-    float hx[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
-    float hv = 0.f, lv = 0.f, hg = 0.f, lg = 0.f;
+// Adjoint accumulators per i particle: U (3) = sum f lam_j, V = sum m_j f,
+// X (3) = sum fp2 (m_i d.lam_j - m_j d.lam_i) d, G = sum f d.lam_j (with dL/dm
+// only).  Float32 partial sums live in registers for one tile; the
+// compensated (hi, lo) totals live in shared memory, lane-contiguous, so that
+// two i particles per lane fit the register budget.
+constexpr int ADJ_NACC = 8;
+constexpr int ADJ_IPL_MAX = 2;
+constexpr int ADJ_COMP_BYTES = ADJ_IPL_MAX * ADJ_NACC * 2 * 32 * 4;
+
+template <int MODE, int IPL>
+struct AccAdj {
+    static constexpr int NACC = MODE == ADJOINT_GM ? 8 : 7;
+    float p[IPL][ADJ_NACC];
+    float *comp;  // [IPL][NACC][hi, lo][32 lanes]
+    int lane;
+    __device__ __forceinline__ float &hi(int u, int k) const { return comp[((u * NACC + k) * 2 + 0) * 32 + lane]; }
+    __device__ __forceinline__ float &lo(int u, int k) const { return comp[((u * NACC + k) * 2 + 1) * 32 + lane]; }
+    __device__ __forceinline__ AccAdj(float *c, int ln) : comp(c), lane(ln)
+    {
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < ADJ_NACC; ++k) p[u][k] = 0.f;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) hi(u, k) = lo(u, k) = 0.f;
+    }
     __device__ __forceinline__ void fold()
     {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            two_sum_acc(hu[k], lu[k], u[k]);
-            two_sum_acc(hx[k], lx[k], x[k]);
-            u[k] = 0.f;
-            x[k] = 0.f;
-        }
-        two_sum_acc(hv, lv, v);
-        two_sum_acc(hg, lg, g);
-        v = 0.f;
-        g = 0.f;
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                float h = hi(u, k), l = lo(u, k);
+                two_sum_acc(h, l, p[u][k]);
+                hi(u, k) = h;
+                lo(u, k) = l;
+                p[u][k] = 0.f;
+            }
     }
+    __device__ __forceinline__ float total(int u, int k) const { return hi(u, k) + lo(u, k); }
 };
 
 // Hardware reciprocal square root (MUFU) without the denormal-input fix-up
@@ -245,9 +269,11 @@ __device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n,
 // fp2 = 2 f_SR'(s):  U += f lam_j ;  V += m_j f ;
 // X += fp2 (m_i (d.lam_j) - m_j (d.lam_i)) d ;  G += f (d.lam_j).
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
+// One pair of the adjoint, accumulated into acc[8] = (U, V, X, G) of one i.
+template <bool GM>
 __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, float oxp, float oyp, float ozp,
                                              float mi, float lix, float liy, float liz, const PairConsts &K,
-                                             Acc<ADJOINT, 1> &A)
+                                             float (&acc)[ADJ_NACC])
 {
     float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
     float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
@@ -262,43 +288,71 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
     float dlj = fmaf(dz, l.z, fmaf(dy, l.y, dx * l.x));
     float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
     float r = fp2 * fmaf(mi, dlj, -(p.w * dli));
-    // the eight accumulations of this pair happen only inside the cutoff
-    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
-        "@p fma.rn.f32 %0, %10, %11, %0;\n\t@p fma.rn.f32 %1, %10, %12, %1;\n\t@p fma.rn.f32 %2, %10, %13, %2;\n\t"
-        "@p fma.rn.f32 %3, %14, %10, %3;\n\t"
-        "@p fma.rn.f32 %4, %15, %16, %4;\n\t@p fma.rn.f32 %5, %15, %17, %5;\n\t@p fma.rn.f32 %6, %15, %18, %6;\n\t"
-        "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
-        : "+f"(A.u[0]), "+f"(A.u[1]), "+f"(A.u[2]), "+f"(A.v), "+f"(A.x[0]), "+f"(A.x[1]), "+f"(A.x[2]),
-          "+f"(A.g)
-        : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
-          "f"(dz), "f"(dlj));
+    // the accumulations of this pair happen only inside the cutoff
+    if constexpr (GM) {
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
+            "@p fma.rn.f32 %0, %10, %11, %0;\n\t@p fma.rn.f32 %1, %10, %12, %1;\n\t@p fma.rn.f32 %2, %10, %13, %2;\n\t"
+            "@p fma.rn.f32 %3, %14, %10, %3;\n\t"
+            "@p fma.rn.f32 %4, %15, %16, %4;\n\t@p fma.rn.f32 %5, %15, %17, %5;\n\t@p fma.rn.f32 %6, %15, %18, %6;\n\t"
+            "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
+            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]),
+              "+f"(acc[7])
+            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
+              "f"(dz), "f"(dlj));
+    } else {
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %7, %8;\n\t"
+            "@p fma.rn.f32 %0, %9, %10, %0;\n\t@p fma.rn.f32 %1, %9, %11, %1;\n\t@p fma.rn.f32 %2, %9, %12, %2;\n\t"
+            "@p fma.rn.f32 %3, %13, %9, %3;\n\t"
+            "@p fma.rn.f32 %4, %14, %15, %4;\n\t@p fma.rn.f32 %5, %14, %16, %5;\n\t@p fma.rn.f32 %6, %14, %17, %6;\n\t}"
+            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6])
+            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
+              "f"(dz));
+    }
 }
 
+// Adjoint pair loop over one staged tile (positions tj, cotangents tl).
+template <int MODE, int IPL>
 __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, const float4 *__restrict__ tl, int n,
-                                             float oxp, float oyp, float ozp, float mi, float lix, float liy,
-                                             float liz, const PairConsts &K, Acc<ADJOINT, 1> &A)
+                                             const float (&op)[IPL][3], const float4 (&oi)[IPL],
+                                             const float4 (&li)[IPL], const PairConsts &K, AccAdj<MODE, IPL> &A)
 {
+    constexpr bool GM = MODE == ADJOINT_GM;
     int j = 0;
     for (; j + 2 <= n; j += 2) {
         const float4 p0 = tj[j], p1 = tj[j + 1], l0 = tl[j], l1 = tl[j + 1];
-        pair_adjoint(p0, l0, oxp, oyp, ozp, mi, lix, liy, liz, K, A);
-        pair_adjoint(p1, l1, oxp, oyp, ozp, mi, lix, liy, liz, K, A);
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            pair_adjoint<GM>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
+            pair_adjoint<GM>(p1, l1, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
+        }
     }
-    if (j < n) pair_adjoint(tj[j], tl[j], oxp, oyp, ozp, mi, lix, liy, liz, K, A);
+    if (j < n) {
+        const float4 p0 = tj[j], l0 = tl[j];
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+            pair_adjoint<GM>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
+    }
 }
 
-// Shared memory of one warp: STAGES tiles (two arrays in the adjoint) and
-// STAGES mbarriers, padded so that every warp's tiles start 128-B aligned.
+// Shared memory of one warp: STAGES tiles (two arrays in the adjoint),
+// STAGES mbarriers and, in the adjoint, the compensated totals; padded so
+// that every warp's tiles start 128-B aligned.
+__host__ __device__ constexpr int warp_tiles_bytes(int mode, int jt, int stages)
+{
+    return stages * (is_adjoint(mode) ? 2 : 1) * jt * 16;
+}
+
 __host__ __device__ constexpr int warp_smem_bytes(int mode, int jt, int stages)
 {
-    return ((stages * (mode == ADJOINT ? 2 : 1) * jt * 16 + stages * 8) + 127) / 128 * 128;
+    return ((warp_tiles_bytes(mode, jt, stages) + stages * 8 + (is_adjoint(mode) ? ADJ_COMP_BYTES : 0)) + 127) / 128 *
+           128;
 }
 
 // Per-warp staging ring: STAGES tiles, their mbarriers and the lifetime tile
 // counters (tile t lives in stage t % STAGES, phase parity (t / STAGES) & 1).
 template <int MODE, int JT, int STAGES>
 struct Ring {
-    static constexpr int NBUF = MODE == ADJOINT ? 2 : 1;
+    static constexpr int NBUF = is_adjoint(MODE) ? 2 : 1;
     float4 *tiles;
     uint64_t *bars;
     uint32_t issued = 0, consumed = 0;
@@ -310,7 +364,7 @@ struct Ring {
         if (lane == 0) {
             const uint32_t st = issued % STAGES;
             tma_issue(bar(st), smem_addr(tile(st)), a.pos + j, (uint32_t)n * 16u, smem_addr(tile(st) + JT),
-                      MODE == ADJOINT ? (const void *)(a.lam + j) : nullptr);
+                      is_adjoint(MODE) ? (const void *)(a.lam + j) : nullptr);
         }
         ++issued;
     }
@@ -332,9 +386,18 @@ struct Ring {
 
 // One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
 // entry of the cell's neighbour list.  Returns false if a wait ran out.
+template <int MODE, int IPL>
+__device__ __forceinline__ auto make_acc(float *comp, int lane)
+{
+    if constexpr (MODE == FORCE)
+        return Acc<FORCE, IPL>();
+    else
+        return AccAdj<MODE, IPL>(comp, lane);
+}
+
 template <int MODE, int JT, int STAGES, int IPL>
-__device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> &ring, int lane, int c, int ib,
-                                         int ie, const hacc_volume &vol)
+__device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> &ring, float *comp, int lane,
+                                         int c, int ib, int ie, const hacc_volume &vol)
 {
     const PairConsts &K = a.k;
     const int n = vol.n;
@@ -351,11 +414,15 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
         active[u] = i < ie;
         oi[u] = active[u] ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float4 li = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (MODE == ADJOINT) {
-        if (active[0]) li = a.lam[ib + lane];
+    float4 li[IPL];
+#pragma unroll
+    for (int u = 0; u < IPL; ++u) {
+        li[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (is_adjoint(MODE)) {
+            if (active[u]) li[u] = a.lam[ib + lane + 32 * u];
+        }
     }
-    Acc<MODE, IPL> A;
+    auto A = make_acc<MODE, IPL>(comp, lane);
 
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
     for (int64_t g0 = e0; g0 < e1; g0 += 32) {
@@ -403,7 +470,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             if constexpr (MODE == FORCE)
                 tile_force<IPL>(tj, cn, op, K, A);
             else
-                tile_adjoint(tj, tj + JT, cn, op[0][0], op[0][1], op[0][2], oi[0].w, li.x, li.y, li.z, K, A);
+                tile_adjoint<MODE, IPL>(tj, tj + JT, cn, op, oi, li, K, A);
             A.fold();
             coff += cn;
             ++ring.consumed;
@@ -423,13 +490,12 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             a.out_y[o] = A.h[u][1] + A.l[u][1];
             a.out_z[o] = A.h[u][2] + A.l[u][2];
         } else {
-            const float U0 = A.hu[0] + A.lu[0], U1 = A.hu[1] + A.lu[1], U2 = A.hu[2] + A.lu[2];
-            const float X0 = A.hx[0] + A.lx[0], X1 = A.hx[1] + A.lx[1], X2 = A.hx[2] + A.lx[2];
-            const float Vs = A.hv + A.lv;
-            a.out_x[o] = fmaf(oi[0].w, U0, fmaf(-li.x, Vs, X0));
-            a.out_y[o] = fmaf(oi[0].w, U1, fmaf(-li.y, Vs, X1));
-            a.out_z[o] = fmaf(oi[0].w, U2, fmaf(-li.z, Vs, X2));
-            if (a.out_m) a.out_m[o] = -(A.hg + A.lg);
+            // dL/dx_i = m_i U - lam_i V + X ;  dL/dm_i = -G
+            const float Vs = A.total(u, 3);
+            a.out_x[o] = fmaf(oi[u].w, A.total(u, 0), fmaf(-li[u].x, Vs, A.total(u, 4)));
+            a.out_y[o] = fmaf(oi[u].w, A.total(u, 1), fmaf(-li[u].y, Vs, A.total(u, 5)));
+            a.out_z[o] = fmaf(oi[u].w, A.total(u, 2), fmaf(-li[u].z, Vs, A.total(u, 6)));
+            if constexpr (MODE == ADJOINT_GM) a.out_m[o] = -A.total(u, 7);
         }
     }
     return true;
@@ -437,8 +503,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
 
 // Persistent work-stealing kernel: each warp takes tasks from a global
 // counter until none is left.  A task of more than 32 particles runs two i
-// particles per lane in the forward pass, and as 32-particle halves in the
-// adjoint.
+// particles per lane.
 template <int MODE, int JT, int STAGES>
 __global__ void __launch_bounds__(256, 3) k_pairs(const KArgs a)
 {
@@ -446,9 +511,12 @@ __global__ void __launch_bounds__(256, 3) k_pairs(const KArgs a)
     constexpr int WARP_BYTES = warp_smem_bytes(MODE, JT, STAGES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + (size_t)warp * WARP_BYTES;
+    constexpr int TILE_BYTES = warp_tiles_bytes(MODE, JT, STAGES);
+    constexpr int COMP_BYTES = is_adjoint(MODE) ? ADJ_COMP_BYTES : 0;
     Ring<MODE, JT, STAGES> ring;
     ring.tiles = reinterpret_cast<float4 *>(wbase);
-    ring.bars = reinterpret_cast<uint64_t *>(wbase + STAGES * Ring<MODE, JT, STAGES>::NBUF * JT * 16);
+    float *comp = reinterpret_cast<float *>(wbase + TILE_BYTES);
+    ring.bars = reinterpret_cast<uint64_t *>(wbase + TILE_BYTES + COMP_BYTES);
 
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
@@ -465,16 +533,11 @@ __global__ void __launch_bounds__(256, 3) k_pairs(const KArgs a)
         if (t >= ntask) break;
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
-        bool ok = true;
-        if constexpr (MODE == FORCE) {
-            if (task.z - task.y > 32)
-                ok = run_task<MODE, JT, STAGES, 2>(a, ring, lane, task.x, task.y, task.z, vol);
-            else
-                ok = run_task<MODE, JT, STAGES, 1>(a, ring, lane, task.x, task.y, task.z, vol);
-        } else {
-            for (int ib = task.y; ib < task.z && ok; ib += 32)
-                ok = run_task<MODE, JT, STAGES, 1>(a, ring, lane, task.x, ib, min(ib + 32, task.z), vol);
-        }
+        bool ok;
+        if (task.z - task.y > 32)
+            ok = run_task<MODE, JT, STAGES, 2>(a, ring, comp, lane, task.x, task.y, task.z, vol);
+        else
+            ok = run_task<MODE, JT, STAGES, 1>(a, ring, comp, lane, task.x, task.y, task.z, vol);
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();
@@ -670,5 +733,6 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     pair_consts(p, a.k);
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(ADJOINT);
+    if (gm) return launch_mode<ADJOINT_GM>(a, L, st);
     return launch_mode<ADJOINT>(a, L, st);
 }

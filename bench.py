@@ -264,18 +264,22 @@ def run_ours(args):
     t_force = statistics.mean(f0[k].elapsed_time(f1[k]) for k in range(args.steps))
     total_pairs = ranks.sum(float(pairs)) * args.steps
     value = total_pairs / (t_ms_max * 1e-3)
+    within = sr.pairs_within_cutoff(prm)  # untimed: the pairs that actually interact
+    total_within = ranks.sum(float(within)) * args.steps
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}", "N": w.N, "volumes": w.V,
-                      "pairs_per_step": pairs, "replicas": ranks.world,
+                      "pairs_per_step": pairs, "pairs_within_cutoff_per_step": within,
+                      "list_efficiency": within / pairs if pairs else None, "replicas": ranks.world,
                       "l2": f"inputs larger than L2 (sorted float4 {16 * w.N / 1e6:.0f} MB + SoA positions "
                             f"{12 * w.N / 1e6:.0f} MB vs 126 MB L2); no flush between steps",
                       "launch": launch.__dict__ if launch else "default", "split_T": split_T,
                       "cuda_graph": graph is not None,
                       "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
-           "gpu_launches": int(launches), "clocks": clk}
+           "gpu_launches": int(launches), "clocks": clk,
+           "within_cutoff_pairs_per_s": total_within / (t_ms_max * 1e-3)}
 
     # roofline of the dominant kernel (the pair force): plain FP32 ALU bound
     props = torch.cuda.get_device_properties(dev)

@@ -233,6 +233,15 @@ int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *binned,
                           float *gm, const hacc_launch *launch, void *ws, size_t ws_bytes,
                           uint32_t *status, void *stream);
 
+/* Counts, into the device int64 *out, the ordered pairs (j != i) that the
+ * pair kernels find inside the cutoff: s + eps < r_c^2 + eps evaluated in
+ * float32 on the cell-relative offsets exactly as hacc_sr_force evaluates it
+ * (the paper's "short-range condition", Sec. III).  With the candidate count
+ * of hacc_build_lists it gives the lists' efficiency.  A reporting tool, not
+ * a hot path (one i per lane, j straight from global memory). */
+int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                     const hacc_sr_params *p, int64_t *out, void *stream);
+
 /* Kick and optional drift of the split-operator step (Eq. 6):
  *   v <- v + dt_kick a;  then, if x != NULL, x <- x + dt_drift v (new v),
  * the drift computed in float64 and rounded once to float32.  If `mesh` is

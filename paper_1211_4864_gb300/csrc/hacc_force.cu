@@ -558,6 +558,52 @@ k_gather_lam(int64_t N, const int32_t *__restrict__ perm, const float *__restric
     }
 }
 
+// Ordered pairs (j != i) inside the cutoff, decided exactly as the pair
+// kernels decide it (same offsets, same float32 s + eps, same compare).  One
+// warp per task, one i per lane, j read straight from global memory: a
+// reporting tool, not a hot path.
+__global__ void __launch_bounds__(256)
+k_count_pairs(const KArgs a, unsigned long long *__restrict__ total)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int ntask = *a.n_tasks;
+    unsigned long long cnt = 0;
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntask; t += warps) {
+        const int4 task = a.tasks[t];
+        const hacc_volume &vol = a.vols[task.w];
+        const int n = vol.n;
+        const float w = vol.w;
+        const double Ld = (double)vol.L;
+        const int64_t lc = (int64_t)task.x - vol.cell_base;
+        const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+        for (int i = task.y + lane; i - lane < task.z; i += 32) {
+            const bool active = i < task.z;
+            const float4 oi = active ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int64_t e = a.nbr_off[task.x]; e < a.nbr_off[task.x + 1]; ++e) {
+                const int cp = a.nbr_cell[e];
+                const int sh = a.nbr_shift[e];
+                const int64_t lp = (int64_t)cp - vol.cell_base;
+                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
+                const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
+                const float Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
+                const float Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
+                const float Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                const float oxp = oi.x - Dx, oyp = oi.y - Dy, ozp = oi.z - Dz;
+                for (int j = a.cell_start[cp]; j < a.cell_start[cp + 1]; ++j) {
+                    const float4 p = a.pos[j];
+                    const float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
+                    const float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, a.k.eps)));
+                    cnt += (active && j != i && se < a.k.rc2e) ? 1ull : 0ull;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(FULL, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(total, cnt);
+}
+
 // poly~(se) = poly(se - eps): c~_m = sum_{k>=m} c_k C(k, m) (-eps)^(k-m), in float64.
 void pair_consts(const hacc_sr_params *p, PairConsts &K)
 {
@@ -735,4 +781,29 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     hacc_launch L = launch ? *launch : default_launch(ADJOINT);
     if (gm) return launch_mode<ADJOINT_GM>(a, L, st);
     return launch_mode<ADJOINT>(a, L, st);
+}
+
+extern "C" int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                                const hacc_sr_params *p, int64_t *out, void *stream)
+{
+    if (!mesh || !binned || !lists || !p || !out || !mesh->vols) return HACC_ERR_INVALID;
+    if (!(p->eps > 0.0f) || !(p->rcut > 0.0f)) return HACC_ERR_INVALID;
+    if (!binned->cell_start || !binned->sorted4 || !lists->nbr_off || !lists->tasks || !lists->n_tasks)
+        return HACC_ERR_INVALID;
+    cudaStream_t st = as_stream(stream);
+    HACC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+    if (mesh->N == 0) return HACC_OK;
+    KArgs a{};
+    a.vols = mesh->vols;
+    a.cell_start = binned->cell_start;
+    a.nbr_off = lists->nbr_off;
+    a.nbr_cell = lists->nbr_cell;
+    a.nbr_shift = lists->nbr_shift;
+    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
+    a.n_tasks = lists->n_tasks;
+    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
+    pair_consts(p, a.k);
+    k_count_pairs<<<num_sms() * 8, 256, 0, st>>>(a, reinterpret_cast<unsigned long long *>(out));
+    HACC_LAUNCH_CHECK();
+    return HACC_OK;
 }

@@ -130,6 +130,12 @@ def hacc_sr_force_adjoint(mesh, binned, lists, params: SRParams, gax, gay, gaz, 
                                             ws.numel(), _ptr(status), _stream()), "hacc_sr_force_adjoint")
 
 
+def hacc_count_pairs(mesh, binned, lists, params: SRParams, out):
+    p = params.c_struct()
+    check(_lib.load().hacc_count_pairs(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
+                                       ctypes.byref(p), _ptr(out), _stream()), "hacc_count_pairs")
+
+
 def hacc_kick(mesh, N, vx, vy, vz, ax, ay, az, dt_kick, x=None, y=None, z=None, dt_drift=0.0):
     check(_lib.load().hacc_kick(ctypes.byref(mesh) if mesh is not None else None, int(N), _ptr(vx), _ptr(vy),
                                 _ptr(vz), _ptr(ax), _ptr(ay), _ptr(az), float(dt_kick), _ptr(x), _ptr(y), _ptr(z),
@@ -252,7 +258,14 @@ class ShortRange:
             raise HaccError(f"device status {s:#x}")
 
     def pair_count(self) -> int:
+        """Candidate ordered pairs (j != i) the pair kernels evaluate."""
         return int(self.n_pairs.item())
+
+    def pairs_within_cutoff(self, params: SRParams) -> int:
+        """Ordered pairs (j != i) inside the cutoff, decided as the pair kernels decide."""
+        out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        hacc_count_pairs(self.mesh, self.binned, self.lists, params, out)
+        return int(out.item())
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,137 @@
+"""Full-size parity in the launch configuration the benchmark times.
+
+At the benchmark sizes the O(N^2) oracle is too slow for every particle, so
+forces and adjoints are compared on seeded samples (random particles plus
+particles of the most crowded cells, chosen from the oracle's own binning);
+binning, lists and tasks are compared bit for bit in full (their oracles are
+linear in N); and properties that hold at any size are checked on every
+particle: Newton's third law for forces, and zero net position gradient
+(translation invariance) for the adjoint.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import MAX_TOL, RMS_TOL, err_norms, need_cuda, sample_targets
+from synth import default_coeffs, make_config
+
+pytestmark = pytest.mark.gpu
+
+
+def _tuned(config):
+    from paper_1211_4864_gb300 import autotune
+    return autotune.cached(config), autotune.cached_split(config, 64), autotune.cached(config, "adjoint")
+
+
+def _setup(config):
+    torch = need_cuda()
+    import paper_1211_4864_gb300 as hs
+    hs.load()
+    w = make_config(config)
+    launch, T, launch_adj = _tuned(config)
+    prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
+    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    m = torch.tensor(w.m, device="cuda")
+    sr.prepare(pos, m)
+    a = sr.force(prm, launch=launch)
+    torch.cuda.synchronize()
+    sr.check_status()
+    return dict(torch=torch, hs=hs, w=w, prm=prm, sr=sr, pos=pos, m=m, a=a, launch=launch, launch_adj=launch_adj)
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    return _setup("clustered256")
+
+
+def _bin_bit_exact(ctx, v=0):
+    w, sr = ctx["w"], ctx["sr"]
+    b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+    ob = oracle.bin_volume(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), w.cell_min)
+    base = int(ctx["table_base"][v]) if "table_base" in ctx else 0
+    n3 = ob["n"] ** 3
+    assert np.array_equal(sr.cell_start.cpu().numpy()[base:base + n3 + 1], ob["cell_start"] + b)
+    assert np.array_equal(sr.perm.cpu().numpy()[b:e], ob["perm"] + b)
+    assert np.array_equal(sr.sorted4.cpu().numpy()[b:e].view(np.int32), ob["sorted4"].view(np.int32))
+    return ob
+
+
+def test_clustered256_binning_lists_tasks_bit_exact(clustered):
+    ob = _bin_bit_exact(clustered)
+    sr = clustered["sr"]
+    off, cell, sh = oracle.lists_volume(ob["n"], ob["w"], 3.0)
+    assert np.array_equal(sr.nbr_off.cpu().numpy(), off)
+    assert np.array_equal(sr.nbr_cell.cpu().numpy(), cell)
+    assert np.array_equal(sr.nbr_shift.cpu().numpy(), sh)
+    t = oracle.tasks(ob["cell_start"], sr.split_T)
+    nt = int(sr.n_tasks.item())
+    assert nt == t.shape[0]
+    assert np.array_equal(sr.tasks.cpu().numpy()[:nt, :3], t)
+
+
+def test_clustered256_forces_sampled(clustered):
+    w, prm = clustered["w"], clustered["prm"]
+    ob = oracle.bin_volume(w.x, w.y, w.z, w.m, float(w.L[0]), w.cell_min)
+    tg = sample_targets(ob["cell_start"], ob["perm"], w.N, 384, crowded_cells=32, per_cell=4, seed=3)
+    ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    got = clustered["a"].cpu().numpy().T[tg].astype(np.float64)
+    rms, mx = err_norms(got, ref)
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+
+
+def test_clustered256_newton_third_law(clustered):
+    sr, m, a = clustered["sr"], clustered["m"], clustered["a"]
+    mom = sr.moments(m, None, a).cpu().numpy()
+    assert np.all(np.abs(mom[3:6]) < 1e-6 * mom[7]), mom
+
+
+def test_clustered256_adjoint_sampled_and_translation_invariant(clustered):
+    torch, w, prm, sr = clustered["torch"], clustered["w"], clustered["prm"], clustered["sr"]
+    rng = np.random.default_rng(21)
+    lam = rng.normal(size=(w.N, 3)).astype(np.float32)
+    g, gm = sr.adjoint(prm, torch.tensor(lam.T.copy(), device="cuda"), launch=clustered["launch_adj"])
+    torch.cuda.synchronize()
+    sr.check_status()
+    G = g.cpu().numpy().T.astype(np.float64)
+    # every particle: the position gradient of a translation-invariant loss sums to zero
+    assert np.linalg.norm(G.sum(0)) < 1e-6 * np.abs(G).sum()
+    tg = rng.choice(w.N, 128, replace=False)
+    rg, rgm = oracle.sr_force_adjoint(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut,
+                                      prm.c.astype(np.float64), lam, tg)
+    rms, _ = err_norms(G[tg], rg)
+    assert rms < RMS_TOL, rms
+    assert np.linalg.norm(gm.cpu().numpy()[tg] - rgm) / np.linalg.norm(rgm) < RMS_TOL
+
+
+def test_lattice128_forces_sampled_and_kick():
+    ctx = _setup("lattice128")
+    w, prm, sr, torch = ctx["w"], ctx["prm"], ctx["sr"], ctx["torch"]
+    _bin_bit_exact(ctx)
+    rng = np.random.default_rng(5)
+    tg = rng.choice(w.N, 1024, replace=False)
+    ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    A = ctx["a"].cpu().numpy().T.astype(np.float64)
+    rms, mx = err_norms(A[tg], ref)
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+    v = torch.zeros_like(ctx["a"])
+    sr.kick(v, ctx["a"], w.dt)
+    torch.cuda.synchronize()
+    assert np.allclose(v.cpu().numpy().T[tg], w.dt * A[tg], rtol=1e-6, atol=0)
+
+
+def test_batched256_sampled_volumes():
+    ctx = _setup("batched256")
+    w, prm, sr = ctx["w"], ctx["prm"], ctx["sr"]
+    ctx["table_base"] = [ctx["sr"].table[v].cell_base for v in range(w.V)]
+    A = ctx["a"].cpu().numpy().T.astype(np.float64)
+    rng = np.random.default_rng(6)
+    for v in sorted(set([0, 127, 128, 255]) | set(rng.choice(w.V, 4, replace=False).tolist())):
+        _bin_bit_exact(ctx, v)
+        b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+        tg = rng.choice(e - b, min(256, e - b), replace=False)
+        ref = oracle.sr_force(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), prm.eps, prm.rcut,
+                              prm.c.astype(np.float64), tg)
+        rms, mx = err_norms(A[b:e][tg], ref)
+        assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)

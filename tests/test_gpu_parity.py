@@ -257,6 +257,24 @@ def test_force_newton3_and_moments(torch, hs):
     assert mom[7] == pytest.approx(np.sum(np.linalg.norm(a, axis=1)), rel=1e-12)
 
 
+@pytest.mark.parametrize("maker", ["uniform", "clustered", "fine"])
+def test_pairs_within_cutoff_count(torch, hs, maker):
+    """The kernels' within-cutoff pair count equals the oracle's brute-force
+    count, up to pairs whose s sits within float32 rounding of r_c^2."""
+    prm = params(hs)
+    if maker == "uniform":
+        w, cm = uniform_box(3000, 14.0, seed=17), 3.0
+    elif maker == "clustered":
+        w, cm = clustered_box(24, 6, seed=12), 3.0
+    else:
+        w, cm = uniform_box(3000, 14.0, seed=18), 1.5
+    sr, _, _, _ = run_force(torch, hs, w, prm, cell_min=cm)
+    got = sr.pairs_within_cutoff(prm)
+    ref = oracle.pair_count(w.x, w.y, w.z, float(w.L[0]), RC)
+    assert abs(got - ref) <= max(2, ref // 1_000_000), (got, ref)
+    assert got <= sr.pair_count()
+
+
 def test_capacity_overflow_sets_status_not_fault(torch, hs):
     w = uniform_box(4096, 16.0, seed=1)
     sr = hs.ShortRange(w.L, w.vol_off, RC)

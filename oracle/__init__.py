@@ -44,43 +44,47 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def configure(L):
+    """Declare the argument and result types of a loaded oracle library."""
+    L.ora_num_threads.restype = ctypes.c_int
+    L.ora_mesh.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    L.ora_bin.argtypes = [_f32p, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          _f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, ctypes.c_float,
+                          ctypes.c_float, _i32p, _i32p, _i32p, _f32p]
+    L.ora_bin.restype = ctypes.c_int
+    L.ora_reach.argtypes = [ctypes.c_float, ctypes.c_float]
+    L.ora_reach.restype = ctypes.c_int32
+    L.ora_lists.argtypes = [ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.ora_lists.restype = ctypes.c_int64
+    L.ora_tasks.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
+    L.ora_tasks.restype = ctypes.c_int64
+    L.ora_fsr.argtypes = [ctypes.c_double, ctypes.c_double, _f64p]
+    L.ora_fsr.restype = ctypes.c_double
+    L.ora_dfsr.argtypes = [ctypes.c_double, ctypes.c_double, _f64p]
+    L.ora_dfsr.restype = ctypes.c_double
+    L.ora_sr_force.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, _f64p, _i64p,
+                               ctypes.c_int64, _f64p, _f64p, _f64p]
+    L.ora_pair_count.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
+                                 ctypes.c_double, _i64p, ctypes.c_int64]
+    L.ora_pair_count.restype = ctypes.c_int64
+    L.ora_sr_force_adjoint.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       _f64p, _f64p, _f64p, _f64p, _i64p, ctypes.c_int64,
+                                       _f64p, _f64p, _f64p, ctypes.c_void_p]
+    L.ora_kick_drift.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_double]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            L.ora_num_threads.restype = ctypes.c_int
-            L.ora_mesh.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_int32),
-                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
-            L.ora_bin.argtypes = [_f32p, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                  _f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, ctypes.c_float,
-                                  ctypes.c_float, _i32p, _i32p, _i32p, _f32p]
-            L.ora_bin.restype = ctypes.c_int
-            L.ora_reach.argtypes = [ctypes.c_float, ctypes.c_float]
-            L.ora_reach.restype = ctypes.c_int32
-            L.ora_lists.argtypes = [ctypes.c_int32, ctypes.c_float, ctypes.c_float,
-                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            L.ora_lists.restype = ctypes.c_int64
-            L.ora_tasks.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
-            L.ora_tasks.restype = ctypes.c_int64
-            L.ora_fsr.argtypes = [ctypes.c_double, ctypes.c_double, _f64p]
-            L.ora_fsr.restype = ctypes.c_double
-            L.ora_dfsr.argtypes = [ctypes.c_double, ctypes.c_double, _f64p]
-            L.ora_dfsr.restype = ctypes.c_double
-            L.ora_sr_force.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_double, _f64p, _i64p,
-                                       ctypes.c_int64, _f64p, _f64p, _f64p]
-            L.ora_pair_count.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
-                                         ctypes.c_double, _i64p, ctypes.c_int64]
-            L.ora_pair_count.restype = ctypes.c_int64
-            L.ora_sr_force_adjoint.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64,
-                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                               _f64p, _f64p, _f64p, _f64p, _i64p, ctypes.c_int64,
-                                               _f64p, _f64p, _f64p, ctypes.c_void_p]
-            L.ora_kick_drift.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
-                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p, ctypes.c_double]
-            _lib = L
+            _lib = configure(ctypes.CDLL(build()))
     return _lib
 
 

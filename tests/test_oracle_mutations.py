@@ -1,0 +1,102 @@
+"""The oracle's pins have teeth: plant a plausible mistake in a copy of the
+oracle's C source, compile it, point the oracle at it, and require that at
+least one pin of tests/test_oracle_pins.py fails.  Each mutant is the kind of
+slip a transcription of the force law, its adjoint, the binning or the lists
+could contain.  All on the CPU (the mistakes are planted in the oracle only).
+"""
+
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "hacc_oracle.c")
+
+# (name, text in the oracle source, replacement)
+MUTANTS = [
+    ("softening dropped", "return pow(s + eps, -1.5) - poly5(c, s);", "return pow(s, -1.5) - poly5(c, s);"),
+    ("pair vector reversed", "d[0] = min_image(x[j] - xi, L);", "d[0] = min_image(xi - x[j], L);"),
+    ("force pair vector reversed", "double dx = min_image(x[j] - xi, L);", "double dx = min_image(xi - x[j], L);"),
+    ("source mass swapped", "double g = m[j] * ora_fsr(s, eps, c);", "double g = m[i] * ora_fsr(s, eps, c);"),
+    ("polynomial index", "s * (c[4] + s * c[5])", "s * (c[4] + s * c[4])"),
+    ("polynomial sign", "return pow(s + eps, -1.5) - poly5(c, s);", "return pow(s + eps, -1.5) + poly5(c, s);"),
+    ("no periodic image", "return d - L * nearbyint(d / L);", "return d;"),
+    ("cutoff not strict", "if (!(s < rc2)) continue;\n            double g", "if (!(s <= rc2)) continue;\n            double g"),
+    ("cutoff radius not squared", "double rc2 = rcut * rcut;\n#pragma omp parallel for schedule(dynamic, 4)\n    for (int64_t t = 0; t < S; ++t) {\n        int64_t i = targets[t];\n        double xi",
+     "double rc2 = rcut;\n#pragma omp parallel for schedule(dynamic, 4)\n    for (int64_t t = 0; t < S; ++t) {\n        int64_t i = targets[t];\n        double xi"),
+    ("derivative exponent", "return -1.5 * pow(s + eps, -2.5) - dpoly5(c, s);",
+     "return -1.5 * pow(s + eps, -1.5) - dpoly5(c, s);"),
+    ("adjoint factor 2 dropped", "double Jlj = f * lj[a] + 2.0 * fp * d[a] * dlj;",
+     "double Jlj = f * lj[a] + fp * d[a] * dlj;"),
+    ("adjoint own-term mass", "g[a] += mi * Jlj - mj * Jli;", "g[a] += mj * Jlj - mj * Jli;"),
+    ("mass gradient sign", "gmi += -f * dlj;", "gmi += f * dlj;"),
+    ("unstable placement", "for (int64_t i = 0; i < N; ++i) {\n        int64_t k = cnt[cell_of[i]]++;",
+     "for (int64_t i = N - 1; i >= 0; --i) {\n        int64_t k = cnt[cell_of[i]]++;"),
+    ("wrap correction dropped", "    if (xw >= L) xw = xw - L;\n    return xw;", "    return xw;"),
+    ("stencil row missing", "for (int dz = -R; dz <= R; ++dz)", "for (int dz = -R; dz < R; ++dz)"),
+    ("image shift sign", "if (px < 0) { px += n; sx = -1; }", "if (px < 0) { px += n; sx = 1; }"),
+    ("cell origin offset", "*o = xw - (float)c * w;", "*o = xw - (float)(c + 1) * w;"),
+    ("drift before kick", "        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += dt_d * vx[i];",
+     "        if (x) x[i] += dt_d * vx[i];\n        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += 0.0;"),
+]
+
+# the pins, fastest first (a mutant stops at its first failing pin)
+PINS = [
+    pins.test_kick_drift_exact_on_dyadic_values,
+    pins.test_softened_newton_closed_form,
+    pins.test_newton_limit_inverse_square,
+    pins.test_polynomial_term_matches_numpy_polyval,
+    pins.test_cutoff_is_exact_zero_and_strict,
+    pins.test_periodic_image_across_boundary,
+    pins.test_superposition_and_mass_linearity,
+    pins.test_brute_force_small_against_independent_numpy,
+    pins.test_perfect_lattice_has_zero_force,
+    pins.test_newton_third_law_and_translation_invariance,
+    pins.test_adjoint_against_finite_differences,
+    pins.test_adjoint_against_torch_float64_autograd,
+    pins.test_binning_invariants_and_numpy_restatement,
+    pins.test_binning_with_displacements_keeps_float64_positions,
+    lambda: pins.test_lists_cover_every_pair_within_cutoff(16.0, 3.0, 3.0),
+    pins.test_trajectory_gradient_against_finite_differences,
+]
+
+
+def _build(src_text, out_dir, tag):
+    c_path = os.path.join(out_dir, f"mut_{tag}.c")
+    so_path = os.path.join(out_dir, f"libmut_{tag}.so")
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-std=c11", "-shared", "-fPIC",
+                           "-o", so_path, c_path, "-lm"])
+    return oracle.configure(ctypes.CDLL(so_path))
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(SRC).read()
+    survivors = []
+    saved = oracle.lib()
+    try:
+        for k, (name, old, new) in enumerate(MUTANTS):
+            assert src.count(old) >= 1, f"mutation site not found: {name}"
+            oracle._lib = _build(src.replace(old, new, 1), str(tmp_path), k)
+            caught = False
+            for pin in PINS:
+                try:
+                    pin()
+                except Exception:  # an assertion, or a numerical blow-up the mistake causes
+                    caught = True
+                    break
+            if not caught:
+                survivors.append(name)
+    finally:
+        oracle._lib = saved
+    assert not survivors, f"mistakes no pin catches: {survivors}"
+
+
+def test_unmutated_oracle_passes_every_pin():
+    for pin in PINS:
+        pin()

@@ -34,8 +34,8 @@ if ROOT not in sys.path:
 FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
 # DRAM bytes of one force launch on clustered256, from ncu (profiles/force_clustered256_dram.md),
 # valid only for the kernel source it was measured on
-FORCE_TRAFFIC = {"workload": "clustered256", "bytes": 2132558592 + 954117632,
-                 "source_sha256": "c10a1a0018f88a2f579e8004dd36adb58b449d23ba327fd76397791cfe2c3994"}
+FORCE_TRAFFIC = {"workload": "clustered256", "bytes": 2135359744 + 954669056,
+                 "source_sha256": "bdbf9e97b5bcdf6404fa932e3933ef6e6ce0d6fac93b51186583535264282613"}
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
 WORKLOADS = {

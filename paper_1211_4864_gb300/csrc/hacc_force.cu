@@ -684,7 +684,8 @@ int check_common(const hacc_mesh *mesh, const hacc_binned *b, const hacc_lists *
     if (!(p->eps > 0.0f) || !isfinite(p->eps) || !(p->rcut > 0.0f) || !isfinite(p->rcut)) return HACC_ERR_INVALID;
     for (int k = 0; k < 6; ++k)
         if (!isfinite(p->c[k])) return HACC_ERR_INVALID;
-    if (!b->cell_start || !b->perm || !b->sorted4 || !aligned16(b->sorted4)) return HACC_ERR_INVALID;
+    if (!b->cell_start) return HACC_ERR_INVALID;
+    if (mesh->N > 0 && (!b->perm || !b->sorted4 || !aligned16(b->sorted4))) return HACC_ERR_INVALID;
     if (!l->nbr_off || !l->n_tasks || (mesh->n_entries > 0 && (!l->nbr_cell || !l->nbr_shift)))
         return HACC_ERR_INVALID;
     if (!l->tasks || !aligned16(l->tasks) || !l->task_order) return HACC_ERR_INVALID;
@@ -788,8 +789,8 @@ extern "C" int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned
 {
     if (!mesh || !binned || !lists || !p || !out || !mesh->vols) return HACC_ERR_INVALID;
     if (!(p->eps > 0.0f) || !(p->rcut > 0.0f)) return HACC_ERR_INVALID;
-    if (!binned->cell_start || !binned->sorted4 || !lists->nbr_off || !lists->tasks || !lists->n_tasks)
-        return HACC_ERR_INVALID;
+    if (!binned->cell_start || !lists->nbr_off || !lists->tasks || !lists->n_tasks) return HACC_ERR_INVALID;
+    if (mesh->N > 0 && !binned->sorted4) return HACC_ERR_INVALID;
     cudaStream_t st = as_stream(stream);
     HACC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
     if (mesh->N == 0) return HACC_OK;

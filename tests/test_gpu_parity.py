@@ -224,6 +224,33 @@ def test_force_edge_cases(torch, hs):
     assert np.max(np.abs(a)) < 1e-5
 
 
+def test_empty_input_and_empty_volume(torch, hs):
+    """N = 0 runs every call and returns nothing; a batch whose middle volume
+    holds no particles bins, lists and forces the others correctly."""
+    prm = params(hs)
+    e = np.zeros(0, np.float32)
+    w0 = Workload("empty", e, e, e, e, e, e, e, np.array([12.0], np.float32), np.array([0, 0], np.int64))
+    sr = hs.ShortRange(w0.L, w0.vol_off, RC)
+    pos = torch.zeros((3, 0), device="cuda")
+    m = torch.zeros(0, device="cuda")
+    sr.prepare(pos, m)
+    a = sr.force(prm)
+    torch.cuda.synchronize()
+    sr.check_status()
+    assert a.shape == (3, 0) and int(sr.n_tasks.item()) == 0 and sr.pair_count() == 0
+    assert np.all(sr.cell_start.cpu().numpy() == 0)
+    # three volumes, the middle one empty
+    wa, wb = uniform_box(700, 10.0, seed=31), uniform_box(900, 11.0, seed=32)
+    cat = lambda f: np.concatenate([getattr(wa, f), getattr(wb, f)])
+    w = Workload("gap", cat("x"), cat("y"), cat("z"), cat("m"), cat("vx"), cat("vy"), cat("vz"),
+                 np.array([10.0, 9.5, 11.0], np.float32), np.array([0, 700, 700, 1600], np.int64))
+    _, _, _, a = run_force(torch, hs, w, prm)
+    for v, ww, (b, e_) in ((0, wa, (0, 700)), (2, wb, (700, 1600))):
+        rms, mx = err_norms(a[b:e_], oracle_force(ww, prm))
+        assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
+    check_bin_lists(torch, hs, w, 3.0, 3.0)
+
+
 def test_force_zero_coefficients_is_truncated_newton(torch, hs):
     w = uniform_box(2000, 12.0, seed=4)
     prm = params(hs, c=np.zeros(6, np.float32), eps=0.05)

@@ -199,7 +199,7 @@ def run_ours(args):
     f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
-    mom = torch.empty(8, dtype=torch.float64, device=dev)
+    mom = torch.empty(9, dtype=torch.float64, device=dev)
     use_graph = args.graph == "on" or (args.graph == "auto" and args.config == "batched256")
 
     def step(k=None):
@@ -397,7 +397,7 @@ def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
     """Same step with inputs in pinned host memory, copies inside the timed region."""
     host_in = torch.tensor(np.stack([w.x, w.y, w.z, w.m, w.vx, w.vy, w.vz]).astype(np.float32)).pin_memory()
     host_out = torch.empty((3, w.N), dtype=torch.float32).pin_memory()
-    host_mom = torch.empty(8, dtype=torch.float64).pin_memory()
+    host_mom = torch.empty(9, dtype=torch.float64).pin_memory()
     dbuf = torch.empty((7, w.N), dtype=torch.float32, device=dev)
     a = torch.empty((3, w.N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()

@@ -233,6 +233,18 @@ int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *binned,
                           float *gm, const hacc_launch *launch, void *ws, size_t ws_bytes,
                           uint32_t *status, void *stream);
 
+/* Short-range potential of every particle, phi [N] in input order:
+ *   phi_i = sum_{j != i, s_ij < r_c^2} m_j V(s_ij),
+ *   V(s) = (r_c^2 + eps)^(-1/2) - (s + eps)^(-1/2) + [P(r_c^2) - P(s)] / 2,
+ *   P(s) = sum_k c_k s^(k+1) / (k+1),
+ * the integral of the force law of Eq. 7 (F = -grad V) that vanishes at the
+ * cutoff; the energy of the short-range sub-cycles of Eq. 6 is then
+ * sum m v^2/2 + sum m phi / 2 (hacc_moments).  Same arithmetic, staging and
+ * arguments as hacc_sr_force. */
+int hacc_sr_potential(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                      const hacc_sr_params *p, float *phi, const hacc_launch *launch, void *ws,
+                      size_t ws_bytes, uint32_t *status, void *stream);
+
 /* Counts, into the device int64 *out, the ordered pairs (j != i) that the
  * pair kernels find inside the cutoff: s + eps < r_c^2 + eps evaluated in
  * float32 on the cell-relative offsets exactly as hacc_sr_force evaluates it
@@ -256,10 +268,12 @@ size_t hacc_moments_workspace_size(int64_t N);
 
 /* Global float64 reductions, in a fixed order (deterministic):
  *   out[0..2] = sum m v,  out[3..5] = sum m a  (zero by Newton's third law),
- *   out[6] = sum m |v|^2 / 2,  out[7] = sum m |a|.   out: device double[8]. */
+ *   out[6] = sum m |v|^2 / 2,  out[7] = sum m |a|,
+ *   out[8] = sum m phi / 2 (the short-range potential energy; each pair once).
+ * Any of v, a, phi may be NULL (its sums are then 0).  out: device double[9]. */
 int hacc_moments(int64_t N, const float *m, const float *vx, const float *vy, const float *vz,
-                 const float *ax, const float *ay, const float *az, double *out, void *ws,
-                 size_t ws_bytes, void *stream);
+                 const float *ax, const float *ay, const float *az, const float *phi, double *out,
+                 void *ws, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -67,6 +67,10 @@ def configure(L):
     L.ora_sr_force.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, _f64p, _i64p,
                                ctypes.c_int64, _f64p, _f64p, _f64p]
+    L.ora_pair_potential.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _f64p]
+    L.ora_pair_potential.restype = ctypes.c_double
+    L.ora_sr_potential.argtypes = [_f64p, _f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, _f64p, _i64p, ctypes.c_int64, _f64p]
     L.ora_pair_count.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_double,
                                  ctypes.c_double, _i64p, ctypes.c_int64]
     L.ora_pair_count.restype = ctypes.c_int64
@@ -187,6 +191,20 @@ def sr_force(x, y, z, m, L, eps, rcut, c, targets=None) -> np.ndarray:
     ax, ay, az = np.zeros(S), np.zeros(S), np.zeros(S)
     lib().ora_sr_force(x, y, z, m, N, float(L), float(eps), float(rcut), _c64(c), t, S, ax, ay, az)
     return np.stack([ax, ay, az], axis=1)
+
+
+def pair_potential(s: float, eps: float, rcut: float, c) -> float:
+    return float(lib().ora_pair_potential(float(s), float(eps), float(rcut), _c64(c)))
+
+
+def sr_potential(x, y, z, m, L, eps, rcut, c, targets=None) -> np.ndarray:
+    """float64 short-range potential phi [S] of the targets (all if None)."""
+    x, y, z, m = _c64(x), _c64(y), _c64(z), _c64(m)
+    N = x.shape[0]
+    t = _targets(N, targets)
+    phi = np.zeros(t.shape[0])
+    lib().ora_sr_potential(x, y, z, m, N, float(L), float(eps), float(rcut), _c64(c), t, t.shape[0], phi)
+    return phi
 
 
 def pair_count(x, y, z, L, rcut, targets=None) -> int:

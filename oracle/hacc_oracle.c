@@ -305,6 +305,44 @@ void ora_sr_force(const double *x, const double *y, const double *z, const doubl
     }
 }
 
+/* Short-range pair potential: the integral of the force law that vanishes at
+ * the cutoff.  With P(s) = sum_k c_k s^(k+1) / (k+1) (so P' = poly):
+ *   V(s) = [(r_c^2 + eps)^-1/2 + P(r_c^2)/2] - [(s + eps)^-1/2 + P(s)/2],
+ * dV/ds = f_SR(s)/2, hence -grad_i of sum_{pairs} m_i m_j V = m_i a_i. */
+static double P6(const double *c, double s)
+{
+    return s * (c[0] + s * (c[1] / 2.0 + s * (c[2] / 3.0 + s * (c[3] / 4.0 + s * (c[4] / 5.0 + s * c[5] / 6.0)))));
+}
+
+double ora_pair_potential(double s, double eps, double rcut, const double *c)
+{
+    double rc2 = rcut * rcut;
+    return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) + 0.5 * P6(c, s));
+}
+
+/* phi_i = sum_{j != i, s_ij < r_c^2} m_j V(s_ij) for the S targets. */
+void ora_sr_potential(const double *x, const double *y, const double *z, const double *m, int64_t N,
+                      double L, double eps, double rcut, const double *c, const int64_t *targets,
+                      int64_t S, double *phi)
+{
+    double rc2 = rcut * rcut;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < S; ++t) {
+        int64_t i = targets[t];
+        double acc = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[j] - x[i], L);
+            double dy = min_image(y[j] - y[i], L);
+            double dz = min_image(z[j] - z[i], L);
+            double s = dx * dx + dy * dy + dz * dz;
+            if (!(s < rc2)) continue;
+            acc += m[j] * ora_pair_potential(s, eps, rcut, c);
+        }
+        phi[t] = acc;
+    }
+}
+
 /* Number of ordered pairs (i, j), j != i, with s_ij < r_c^2. */
 int64_t ora_pair_count(const double *x, const double *y, const double *z, int64_t N,
                        double L, double rcut, const int64_t *targets, int64_t S)

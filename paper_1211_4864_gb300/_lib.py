@@ -91,7 +91,9 @@ SIGNATURES = {
     "hacc_kick": (ctypes.c_int, [_PS(hacc_mesh), ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_float,
                                  _P, _P, _P, ctypes.c_float, _P]),
     "hacc_moments_workspace_size": (ctypes.c_size_t, [ctypes.c_int64]),
-    "hacc_moments": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "hacc_moments": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "hacc_sr_potential": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists), _PS(hacc_sr_params),
+                                         _P, _PS(hacc_launch), _P, ctypes.c_size_t, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -32,15 +32,17 @@ constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 constexpr uint32_t WAIT_HINT_NS = 100000;  // a waiting warp may sleep up to 0.1 ms per try
 
 // FORCE: accelerations.  ADJOINT: dL/dx.  ADJOINT_GM: dL/dx and dL/dm.
-enum Mode { FORCE = 0, ADJOINT = 1, ADJOINT_GM = 2 };
+// POTENTIAL: the short-range potential of each particle.
+enum Mode { FORCE = 0, ADJOINT = 1, ADJOINT_GM = 2, POTENTIAL = 3 };
 
-__host__ __device__ constexpr bool is_adjoint(int mode) { return mode != FORCE; }
+__host__ __device__ constexpr bool is_adjoint(int mode) { return mode == ADJOINT || mode == ADJOINT_GM; }
 
 struct PairConsts {
     float eps;      // softening
     float rc2e;     // r_c^2 + eps (cut on se = s + eps)
     float nc[6];    // -(coefficients of poly~ in se), for f
     float kp[5];    // -2 (k+1) c~_{k+1}: Horner coefficients of -2 poly~'(se)
+    float pv[7];    // pair potential V = pv(se) - (se)^-1/2: degree-6 coefficients in se
 };
 
 struct KArgs {
@@ -147,27 +149,33 @@ __device__ __forceinline__ bool next_tile(int ng, int cnt, int &k, int &off, int
 template <int MODE, int IPL>
 struct Acc;
 
-template <int IPL>
-struct Acc<FORCE, IPL> {
-    float a[IPL][3], h[IPL][3], l[IPL][3];
-    __device__ __forceinline__ Acc()
+template <int IPL, int NC>
+struct AccN {
+    float a[IPL][NC], h[IPL][NC], l[IPL][NC];
+    __device__ __forceinline__ AccN()
     {
 #pragma unroll
         for (int u = 0; u < IPL; ++u)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) a[u][k] = h[u][k] = l[u][k] = 0.f;
+            for (int k = 0; k < NC; ++k) a[u][k] = h[u][k] = l[u][k] = 0.f;
     }
     __device__ __forceinline__ void fold()
     {
 #pragma unroll
         for (int u = 0; u < IPL; ++u)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < NC; ++k) {
                 two_sum_acc(h[u][k], l[u][k], a[u][k]);
                 a[u][k] = 0.f;
             }
     }
 };
+
+template <int IPL>
+struct Acc<FORCE, IPL> : AccN<IPL, 3> {};
+
+template <int IPL>
+struct Acc<POTENTIAL, IPL> : AccN<IPL, 1> {};
 
 // Adjoint accumulators per i particle: U (3) = sum f lam_j, V = sum m_j f,
 // X (3) = sum fp2 (m_i d.lam_j - m_j d.lam_i) d, G = sum f d.lam_j (with dL/dm
@@ -262,6 +270,49 @@ __device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n,
         const float4 p = tj[j];
 #pragma unroll
         for (int u = 0; u < IPL; ++u) pair_force(p, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+    }
+}
+
+// The short-range pair potential V(s) = pv(se) - (s + eps)^-1/2 (se = s + eps):
+// the integral of the force law, zero at the cutoff (F = -grad V).
+__device__ __forceinline__ float pair_potential_of(float se, const PairConsts &K)
+{
+    const float h = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(K.pv[6], se, K.pv[5]), se, K.pv[4]), se, K.pv[3]), se, K.pv[2]),
+                              se, K.pv[1]),
+                         se, K.pv[0]);
+    return h - rsqrt_hw(se);
+}
+
+__device__ __forceinline__ void pair_potential(const float4 p, float oxp, float oyp, float ozp, const PairConsts &K,
+                                               float *acc)
+{
+    float dx = p.x - oxp, dy = p.y - oyp, dz = p.z - ozp;
+    float se = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, K.eps)));
+    float v = pair_potential_of(se, K);
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %1, %2;\n\t@p fma.rn.f32 %0, %3, %4, %0;\n\t}"
+        : "+f"(acc[0])
+        : "f"(se), "f"(K.rc2e), "f"(p.w), "f"(v));
+}
+
+template <int IPL>
+__device__ __forceinline__ void tile_potential(const float4 *__restrict__ tj, int n, const float (&op)[IPL][3],
+                                               const PairConsts &K, Acc<POTENTIAL, IPL> &A)
+{
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+        const float4 p0 = tj[j], p1 = tj[j + 1], p2 = tj[j + 2], p3 = tj[j + 3];
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            pair_potential(p0, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_potential(p1, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_potential(p2, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_potential(p3, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+        }
+    }
+    for (; j < n; ++j) {
+        const float4 p = tj[j];
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) pair_potential(p, op[u][0], op[u][1], op[u][2], K, A.a[u]);
     }
 }
 
@@ -389,8 +440,8 @@ struct Ring {
 template <int MODE, int IPL>
 __device__ __forceinline__ auto make_acc(float *comp, int lane)
 {
-    if constexpr (MODE == FORCE)
-        return Acc<FORCE, IPL>();
+    if constexpr (MODE == FORCE || MODE == POTENTIAL)
+        return Acc<MODE, IPL>();
     else
         return AccAdj<MODE, IPL>(comp, lane);
 }
@@ -469,6 +520,8 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             const float4 *tj = ring.tile(ring.consumed % STAGES);
             if constexpr (MODE == FORCE)
                 tile_force<IPL>(tj, cn, op, K, A);
+            else if constexpr (MODE == POTENTIAL)
+                tile_potential<IPL>(tj, cn, op, K, A);
             else
                 tile_adjoint<MODE, IPL>(tj, tj + JT, cn, op, oi, li, K, A);
             A.fold();
@@ -489,6 +542,10 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             a.out_x[o] = A.h[u][0] + A.l[u][0];
             a.out_y[o] = A.h[u][1] + A.l[u][1];
             a.out_z[o] = A.h[u][2] + A.l[u][2];
+        } else if constexpr (MODE == POTENTIAL) {
+            // the sum met particle i itself once (d = 0, se = eps exactly): take that term out
+            const float self = pair_potential_of(K.eps, K);
+            a.out_x[o] = (A.h[u][0] + A.l[u][0]) - oi[u].w * self;
         } else {
             // dL/dx_i = m_i U - lam_i V + X ;  dL/dm_i = -G
             const float Vs = A.total(u, 3);
@@ -621,6 +678,23 @@ void pair_consts(const hacc_sr_params *p, PairConsts &K)
     K.rc2e = (float)((double)p->rcut * (double)p->rcut + (double)p->eps);
     for (int k = 0; k < 6; ++k) K.nc[k] = (float)(-ct[k]);
     for (int k = 0; k < 5; ++k) K.kp[k] = (float)(-2.0 * (k + 1) * ct[k + 1]);
+    // potential: V(s) = C0 - (s + eps)^-1/2 - P(s) / 2 with P(s) = sum_k c_k s^(k+1) / (k+1),
+    // C0 = (rc^2 + eps)^-1/2 + P(rc^2) / 2 so that V(rc^2) = 0; expanded in se = s + eps
+    double Pm[7] = {0, 0, 0, 0, 0, 0, 0};  // P(s) = sum_m Pm[m] s^m
+    for (int k = 0; k < 6; ++k) Pm[k + 1] = c[k] / (double)(k + 1);
+    const double rc2 = (double)p->rcut * (double)p->rcut;
+    double Prc = 0.0;
+    for (int mdeg = 6; mdeg >= 1; --mdeg) Prc = (Prc + Pm[mdeg]) * rc2;
+    const double C0 = 1.0 / sqrt(rc2 + (double)p->eps) + 0.5 * Prc;
+    for (int jdeg = 0; jdeg <= 6; ++jdeg) {
+        double acc = 0.0;
+        for (int mdeg = jdeg; mdeg <= 6; ++mdeg) {
+            double bin = 1.0;  // C(mdeg, jdeg)
+            for (int q = 0; q < jdeg; ++q) bin = bin * (double)(mdeg - q) / (double)(q + 1);
+            acc += -0.5 * Pm[mdeg] * bin * pow(e, (double)(mdeg - jdeg));
+        }
+        K.pv[jdeg] = (float)(acc + (jdeg == 0 ? C0 : 0.0));
+    }
 }
 
 struct ForceWs {
@@ -782,6 +856,36 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     hacc_launch L = launch ? *launch : default_launch(ADJOINT);
     if (gm) return launch_mode<ADJOINT_GM>(a, L, st);
     return launch_mode<ADJOINT>(a, L, st);
+}
+
+extern "C" int hacc_sr_potential(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                                 const hacc_sr_params *p, float *phi, const hacc_launch *launch, void *ws,
+                                 size_t ws_bytes, uint32_t *status, void *stream)
+{
+    int rc = check_common(mesh, binned, lists, p, launch, ws, ws_bytes, status);
+    if (rc) return rc;
+    if (mesh->N > 0 && !phi) return HACC_ERR_INVALID;
+    if (mesh->N == 0) return HACC_OK;
+    cudaStream_t st = as_stream(stream);
+    ForceWs F = force_layout(mesh, ws);
+    KArgs a{};
+    a.vols = mesh->vols;
+    a.cell_start = binned->cell_start;
+    a.nbr_off = lists->nbr_off;
+    a.nbr_cell = lists->nbr_cell;
+    a.nbr_shift = lists->nbr_shift;
+    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
+    a.order = lists->task_order;
+    a.n_tasks = lists->n_tasks;
+    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
+    a.perm = binned->perm;
+    a.out_x = phi;
+    a.counter = F.counter;
+    a.status = status;
+    pair_consts(p, a.k);
+    HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
+    hacc_launch L = launch ? *launch : default_launch(FORCE);
+    return launch_mode<POTENTIAL>(a, L, st);
 }
 
 extern "C" int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,

@@ -1,5 +1,6 @@
 // Kick / drift maps of the split-operator step (Eq. 6 of the paper) and the
-// float64 global reductions (momentum, Newton-III residual, kinetic energy).
+// float64 global reductions (momentum, Newton-III residual, kinetic and
+// short-range potential energy).
 #include "hacc_common.cuh"
 
 namespace hacc {
@@ -46,6 +47,7 @@ k_kick(int64_t N, float *__restrict__ vx, float *__restrict__ vy, float *__restr
 
 constexpr int MOM_THREADS = 256;
 constexpr int MOM_BLOCKS = 1024;
+constexpr int MOM_N = 9;  // sums: m v (3), m a (3), kinetic, m |a|, potential
 
 __device__ __forceinline__ double block_sum(double v, double *sh)
 {
@@ -66,10 +68,10 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 __global__ void __launch_bounds__(MOM_THREADS)
 k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restrict__ vx, const float *__restrict__ vy,
                   const float *__restrict__ vz, const float *__restrict__ ax, const float *__restrict__ ay,
-                  const float *__restrict__ az, double *__restrict__ part)
+                  const float *__restrict__ az, const float *__restrict__ phi, double *__restrict__ part)
 {
     __shared__ double sh[MOM_THREADS / 32];
-    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double s[MOM_N] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x; i < N; i += (int64_t)MOM_BLOCKS * MOM_THREADS) {
         const double mi = m[i];
         const double v0 = vx ? vx[i] : 0.0, v1 = vy ? vy[i] : 0.0, v2 = vz ? vz[i] : 0.0;
@@ -82,9 +84,10 @@ k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restric
         s[5] += mi * a2;
         s[6] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
         s[7] += mi * sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+        s[8] += phi ? 0.5 * mi * (double)phi[i] : 0.0;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < MOM_N; ++k) {
         double r = block_sum(s[k], sh);
         if (threadIdx.x == 0) part[(int64_t)k * MOM_BLOCKS + blockIdx.x] = r;
     }
@@ -93,7 +96,7 @@ k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restric
 __global__ void __launch_bounds__(MOM_THREADS) k_moments_final(const double *__restrict__ part, double *__restrict__ out)
 {
     __shared__ double sh[MOM_THREADS / 32];
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < MOM_N; ++k) {
         double s = 0.0;
         for (int b = threadIdx.x; b < MOM_BLOCKS; b += MOM_THREADS) s += part[(int64_t)k * MOM_BLOCKS + b];
         double r = block_sum(s, sh);
@@ -126,18 +129,18 @@ extern "C" int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy,
 extern "C" size_t hacc_moments_workspace_size(int64_t N)
 {
     (void)N;
-    return (size_t)8 * MOM_BLOCKS * sizeof(double);
+    return (size_t)MOM_N * MOM_BLOCKS * sizeof(double);
 }
 
 extern "C" int hacc_moments(int64_t N, const float *m, const float *vx, const float *vy, const float *vz,
-                            const float *ax, const float *ay, const float *az, double *out, void *ws,
-                            size_t ws_bytes, void *stream)
+                            const float *ax, const float *ay, const float *az, const float *phi, double *out,
+                            void *ws, size_t ws_bytes, void *stream)
 {
     if (N < 0 || !out || !ws) return HACC_ERR_INVALID;
     if (N > 0 && !m) return HACC_ERR_INVALID;
     if (ws_bytes < hacc_moments_workspace_size(N)) return HACC_ERR_CAPACITY;
     cudaStream_t st = as_stream(stream);
-    k_moments_partial<<<MOM_BLOCKS, MOM_THREADS, 0, st>>>(N, m, vx, vy, vz, ax, ay, az,
+    k_moments_partial<<<MOM_BLOCKS, MOM_THREADS, 0, st>>>(N, m, vx, vy, vz, ax, ay, az, phi,
                                                           reinterpret_cast<double *>(ws));
     HACC_LAUNCH_CHECK();
     k_moments_final<<<1, MOM_THREADS, 0, st>>>(reinterpret_cast<const double *>(ws), out);

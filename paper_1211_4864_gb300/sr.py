@@ -142,9 +142,17 @@ def hacc_kick(mesh, N, vx, vy, vz, ax, ay, az, dt_kick, x=None, y=None, z=None, 
                                 float(dt_drift), _stream()), "hacc_kick")
 
 
-def hacc_moments(N, m, vx, vy, vz, ax, ay, az, out, ws):
+def hacc_moments(N, m, vx, vy, vz, ax, ay, az, out, ws, phi=None):
     check(_lib.load().hacc_moments(int(N), _ptr(m), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(ax), _ptr(ay), _ptr(az),
-                                   _ptr(out), _ptr(ws), ws.numel(), _stream()), "hacc_moments")
+                                   _ptr(phi), _ptr(out), _ptr(ws), ws.numel(), _stream()), "hacc_moments")
+
+
+def hacc_sr_potential(mesh, binned, lists, params: SRParams, phi, ws, status, launch: Launch | None = None):
+    p = params.c_struct()
+    lc = launch.c_struct() if launch is not None else None
+    check(_lib.load().hacc_sr_potential(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
+                                        ctypes.byref(p), _ptr(phi), ctypes.byref(lc) if lc else None, _ptr(ws),
+                                        ws.numel(), _ptr(status), _stream()), "hacc_sr_potential")
 
 
 # ---------------------------------------------------------------------------
@@ -235,15 +243,39 @@ class ShortRange:
             hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], a[0], a[1], a[2], dt_kick, pos[0],
                       pos[1], pos[2], dt_drift)
 
-    def moments(self, m, v=None, a=None):
-        out = torch.empty(8, dtype=torch.float64, device=self.device)
+    def moments(self, m, v=None, a=None, phi=None):
+        """FP64 [sum m v (3), sum m a (3), kinetic energy, sum m |a|, potential energy]."""
+        out = torch.empty(9, dtype=torch.float64, device=self.device)
         vx = vy = vz = ax = ay = az = None
         if v is not None:
             vx, vy, vz = v[0], v[1], v[2]
         if a is not None:
             ax, ay, az = a[0], a[1], a[2]
-        hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.ws)
+        hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.ws, phi)
         return out
+
+    def potential(self, params: SRParams, out=None, launch: Launch | None = None):
+        """Short-range potential phi [N] of every particle (same binning and lists as force)."""
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        hacc_sr_potential(self.mesh, self.binned, self.lists, params, out, self.ws, self.status, launch)
+        return out
+
+    def sks_subcycles(self, pos, v, m, params: SRParams, h: float, n_c: int, a=None,
+                      launch: Launch | None = None):
+        """n_c short-range sub-cycles S(h/2) K(h) S(h/2) of the split-operator
+        step (Eq. 6), in place on pos [3, N] (wrapped into the boxes) and
+        v [3, N]: stream h/2, re-bin, force, kick h, stream h/2.  Every call
+        is a library kernel, so the sequence can be captured in a CUDA graph."""
+        if a is None:
+            a = torch.empty_like(v)
+        zero = a  # dt_kick = 0: the stream map leaves v unchanged
+        for _ in range(n_c):
+            self.kick(v, zero, 0.0, pos, 0.5 * h)
+            self.prepare(pos, m)
+            self.force(params, a, launch=launch)
+            self.kick(v, a, h, pos, 0.5 * h)
+        return a
 
     def prepare(self, pos, m, disp=None):
         """Binning and lists for positions pos [3, N] (plus displacements disp

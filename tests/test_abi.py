@@ -118,5 +118,5 @@ def test_device_calls_reject_bad_arguments_on_host(lib):
                         None) == _lib.HACC_ERR_INVALID
     assert lib.hacc_kick(None, -1, None, None, None, None, None, None, 0.0, None, None, None, 0.0,
                          None) == _lib.HACC_ERR_INVALID
-    assert lib.hacc_moments(5, None, None, None, None, None, None, None, None, None, 0,
+    assert lib.hacc_moments(5, None, None, None, None, None, None, None, None, None, None, 0,
                             None) == _lib.HACC_ERR_INVALID

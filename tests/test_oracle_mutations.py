@@ -40,6 +40,9 @@ MUTANTS = [
     ("stencil row missing", "for (int dz = -R; dz <= R; ++dz)", "for (int dz = -R; dz < R; ++dz)"),
     ("image shift sign", "if (px < 0) { px += n; sx = -1; }", "if (px < 0) { px += n; sx = 1; }"),
     ("cell origin offset", "*o = xw - (float)c * w;", "*o = xw - (float)(c + 1) * w;"),
+    ("potential sign", "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) + 0.5 * P6(c, s));",
+     "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) - 0.5 * P6(c, s));"),
+    ("potential polynomial index", "s * (c[4] / 5.0 + s * c[5] / 6.0)", "s * (c[4] / 5.0 + s * c[5] / 5.0)"),
     ("drift before kick", "        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += dt_d * vx[i];",
      "        if (x) x[i] += dt_d * vx[i];\n        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += 0.0;"),
 ]
@@ -56,6 +59,8 @@ PINS = [
     pins.test_brute_force_small_against_independent_numpy,
     pins.test_perfect_lattice_has_zero_force,
     pins.test_newton_third_law_and_translation_invariance,
+    pins.test_potential_closed_form_and_cutoff,
+    pins.test_force_is_minus_gradient_of_potential_energy,
     pins.test_adjoint_against_finite_differences,
     pins.test_adjoint_against_torch_float64_autograd,
     pins.test_binning_invariants_and_numpy_restatement,

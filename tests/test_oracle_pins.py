@@ -158,6 +158,45 @@ def test_brute_force_small_against_independent_numpy():
     assert oracle.pair_count(p[:, 0], p[:, 1], p[:, 2], L, RC) == int(mask.sum())
 
 
+def test_potential_closed_form_and_cutoff():
+    """c = 0: V(s) = (r_c^2 + eps)^-1/2 - (s + eps)^-1/2 (softened Newton, shifted
+    to vanish at r_c); and V(r_c^2) = 0 for any coefficients."""
+    for r, eps in [(0.5, 0.01), (2.0, 0.3)]:
+        x, y, z, m, L = _two((4.0, 4.0, 4.0), (4.0 + r, 4.0, 4.0), m1=1.0, m2=2.0)
+        phi = oracle.sr_potential(x, y, z, m, L, eps, RC, np.zeros(6))
+        expect = (RC * RC + eps) ** -0.5 - (r * r + eps) ** -0.5
+        assert phi[0] == pytest.approx(2.0 * expect, rel=1e-13)
+        assert phi[1] == pytest.approx(expect, rel=1e-13)
+    rng = np.random.default_rng(8)
+    assert abs(oracle.pair_potential(RC * RC, EPS, RC, rng.normal(size=6))) < 1e-13
+
+
+def test_force_is_minus_gradient_of_potential_energy():
+    """E = sum_i m_i phi_i / 2 and -dE/dx_i = m_i a_i (finite differences):
+    ties the potential to the force law without retyping either."""
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(9)
+    L, N = 7.0, 60
+    while True:
+        p = rng.random((N, 3)) * L
+        if _pairs_clear_of_cutoff(p, L, 1e-3):
+            break
+    m = rng.uniform(0.5, 1.5, N)
+
+    def E(pp):
+        return 0.5 * float(np.sum(m * oracle.sr_potential(pp[:, 0], pp[:, 1], pp[:, 2], m, L, EPS, RC, c)))
+
+    a = oracle.sr_force(p[:, 0], p[:, 1], p[:, 2], m, L, EPS, RC, c)
+    h = 1e-6
+    for i in [0, 13, 44]:
+        for k in range(3):
+            pp, pm = p.copy(), p.copy()
+            pp[i, k] += h
+            pm[i, k] -= h
+            g = (E(pp) - E(pm)) / (2 * h)
+            assert -g == pytest.approx(m[i] * a[i, k], rel=1e-6, abs=1e-8)
+
+
 # --------------------------------------------------------------------------
 # adjoint
 # --------------------------------------------------------------------------

@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--graph", choices=["auto", "on", "off"], default="auto",
                     help="replay the step as one captured CUDA graph (auto: on for batched256)")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
+    ap.add_argument("--no-sks", action="store_true", help="skip the sub-cycle (SKS) measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the step: force-kernel rate vs neighbour-list length and occupancy")
     return ap.parse_args()
 
 
@@ -320,6 +323,10 @@ def run_ours(args):
     if not args.no_diff and ranks.rank == 0:
         out["differentiation"] = differentiation(torch, hs)
 
+    # short-range sub-cycles of the split-operator step: throughput and drift
+    if not args.no_sks and ranks.rank == 0:
+        out["sks"] = sks_measure(torch, hs)
+
     # end to end through the public API with host buffers
     if not args.no_e2e:
         out["e2e"] = e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs)
@@ -391,6 +398,58 @@ def force_traffic(config: str):
     if config != FORCE_TRAFFIC["workload"] or sha != FORCE_TRAFFIC["source_sha256"]:
         return None
     return FORCE_TRAFFIC["bytes"]
+
+
+def sks_measure(torch, hs, n_c: int = 10, h: float = 0.01):
+    """lattice128 with seeded thermal velocities (rms 0.1 per axis): n_c sub-cycles
+    S(h/2) K(h) S(h/2) (Eq. 6) captured once as a CUDA graph and replayed; reports
+    time per sub-cycle and the drift of total energy and momentum (FP64 sums)."""
+    from paper_1211_4864_gb300 import autotune
+    from synth import default_coeffs, make_config
+    w = make_config("lattice128")
+    prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
+    sr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=autotune.cached_split("lattice128", 64))
+    launch = autotune.cached("lattice128")
+    rng = np.random.default_rng(77)
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    v = torch.tensor((rng.normal(size=(3, w.N)) * 0.1).astype(np.float32), device="cuda")
+    m = torch.tensor(w.m, device="cuda")
+    a = torch.empty_like(v)
+
+    def energy():
+        sr.prepare(pos, m)
+        phi = sr.potential(prm, launch=launch)
+        mom = sr.moments(m, v, None, phi).cpu().numpy()
+        return float(mom[6] + mom[8]), mom[0:3].copy()
+
+    e0, p0 = energy()
+    sr.sks_subcycles(pos, v, m, prm, h, 1, a, launch=launch)  # warm-up outside capture
+    e0, p0 = energy()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        pos_in, v_in = pos.clone(), v.clone()
+        with torch.cuda.graph(g, stream=side):
+            sr.sks_subcycles(pos, v, m, prm, h, n_c, a, launch=launch)
+    torch.cuda.current_stream().wait_stream(side)
+    pos.copy_(pos_in)
+    v.copy_(v_in)
+    torch.cuda.synchronize()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_a.record()
+    g.replay()
+    e_b.record()
+    torch.cuda.synchronize()
+    sr.check_status()
+    t = e_a.elapsed_time(e_b)
+    e1, p1 = energy()
+    pairs = sr.pair_count()
+    return {"workload": "lattice128 (2,097,152 particles) with N(0, 0.1^2) velocities per axis (seed 77), "
+                        f"{n_c} sub-cycles of h = {h}, one captured CUDA graph",
+            "ms_per_subcycle": t / n_c, "pairs_per_s": pairs * n_c / (t * 1e-3),
+            "energy_start": e0, "energy_end": e1, "relative_energy_drift": (e1 - e0) / abs(e0),
+            "momentum_drift": float(np.linalg.norm(p1 - p0))}
 
 
 def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
@@ -516,10 +575,58 @@ def run_reference(args):
     ranks.close()
 
 
+def sweep(args):
+    """Force-kernel rate vs neighbour-list length and resident CTAs per SM: the
+    GPU analogue of the paper's threading study (Fig. 5: kernel performance vs
+    ranks x threads per node and neighbour-list size 500-2500).  Uniform boxes
+    of side 96 at densities 0.6-3 particles per grid cell cubed give 440-2200
+    candidate neighbours per particle with r_c = 3."""
+    import torch
+
+    import paper_1211_4864_gb300 as hs
+    from synth import default_coeffs, uniform_box
+    hs.load()
+    prm = hs.SRParams(0.01, 3.0, default_coeffs())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * 2070e6
+    rows = []
+    for rho in (0.6, 1.0, 1.5, 2.0, 3.0):
+        n = int(round(rho * 96 ** 3))
+        w = uniform_box(n, 96.0, seed=90)
+        pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+        m = torch.tensor(w.m, device="cuda")
+        for T in (32, 64):
+            sr = hs.ShortRange(w.L, w.vol_off, 3.0, split_T=T)
+            sr.prepare(pos, m)
+            torch.cuda.synchronize()
+            pairs = sr.pair_count()
+            out = torch.empty((3, n), device="cuda")
+            for cps in (1, 2, 3):
+                L = hs.Launch(8, cps, 128, 2)
+                sr.force(prm, out, launch=L)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(5):
+                    sr.force(prm, out, launch=L)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 5
+                rows.append({"density": rho, "list_length": pairs / n, "split_T": T, "ctas_per_sm": cps,
+                             "warps_per_sm": 8 * cps, "ms": t, "pairs_per_s": pairs / (t * 1e-3),
+                             "frac_fp32_peak": FLOPS_PER_PAIR * pairs / (t * 1e-3) / peak})
+            sr.check_status()
+            del sr
+            torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "force rate vs neighbour-list length and occupancy", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        sweep(args)
     else:
         run_ours(args)
 

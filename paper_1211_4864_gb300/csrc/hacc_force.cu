@@ -86,23 +86,21 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok;
 }
 
-// Lane 0 only: expect `bytes` on the barrier and start the bulk copies.
-__device__ __forceinline__ void tma_issue(uint32_t bar, uint32_t dst, const void *src, uint32_t bytes,
-                                          uint32_t dst2, const void *src2)
+// Lane 0 only: pieces of a multi-segment tile.  Each bulk copy first raises
+// the barrier's expected byte count; one arrive after the last copy ends the
+// tile, so the phase cannot complete before every copy was issued.
+__device__ __forceinline__ void tma_expect_copy(uint32_t bar, uint32_t dst, const void *src, uint32_t bytes)
 {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    uint32_t total = src2 ? 2 * bytes : bytes;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
-    if (src2)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                dst2),
-            "l"(src2), "r"(bytes), "r"(bar)
-            : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // All lanes wait for a barrier phase; false (uniformly) if it ran out of time.
@@ -127,22 +125,6 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b)
     lo = __fadd_rn(lo, err);
 }
 
-// Next non-empty tile of the group at or after (k, off); entry counts live in
-// lane k's `cnt`.  Warp-uniform.
-template <int JT>
-__device__ __forceinline__ bool next_tile(int ng, int cnt, int &k, int &off, int &n)
-{
-    while (k < ng) {
-        int c = __shfl_sync(FULL, cnt, k);
-        if (off < c) {
-            n = min(JT, c - off);
-            return true;
-        }
-        ++k;
-        off = 0;
-    }
-    return false;
-}
 
 // Per-lane accumulators of IPL i particles: float32 within a tile, then
 // folded into a compensated (hi, lo) pair.
@@ -369,21 +351,22 @@ __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, cons
 {
     constexpr bool GM = MODE == ADJOINT_GM;
     int j = 0;
-    for (; j + 2 <= n; j += 2) {
-        const float4 p0 = tj[j], p1 = tj[j + 1], l0 = tl[j], l1 = tl[j + 1];
-#pragma unroll
-        for (int u = 0; u < IPL; ++u) {
-            pair_adjoint<GM>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
-            pair_adjoint<GM>(p1, l1, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
+    if constexpr (IPL == 1) {
+        // one i per lane: two j per trip for independent work
+        for (; j + 2 <= n; j += 2) {
+            const float4 p0 = tj[j], p1 = tj[j + 1], l0 = tl[j], l1 = tl[j + 1];
+            pair_adjoint<GM>(p0, l0, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K, A.p[0]);
+            pair_adjoint<GM>(p1, l1, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K, A.p[0]);
         }
     }
-    if (j < n) {
+    for (; j < n; ++j) {
         const float4 p0 = tj[j], l0 = tl[j];
 #pragma unroll
         for (int u = 0; u < IPL; ++u)
             pair_adjoint<GM>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
     }
 }
+
 
 // Shared memory of one warp: STAGES tiles (two arrays in the adjoint),
 // STAGES mbarriers and, in the adjoint, the compensated totals; padded so
@@ -409,15 +392,41 @@ struct Ring {
     uint32_t issued = 0, consumed = 0;
     __device__ __forceinline__ float4 *tile(uint32_t st) const { return tiles + (size_t)st * NBUF * JT; }
     __device__ __forceinline__ uint32_t bar(uint32_t st) const { return smem_addr(&bars[st]); }
-    // lane 0 starts the copy of n records at j (positions, plus cotangents in the adjoint)
-    __device__ __forceinline__ void issue(const KArgs &a, int lane, int j, int n)
+    // Stage the next tile: consecutive pieces of the group's entries (entry
+    // counts in lane k's `cnt`, first records in lane k's `jb`) until JT
+    // records or the group is exhausted, one bulk copy per piece (plus the
+    // cotangents in the adjoint).  Warp-uniform; false if nothing was left.
+    __device__ __forceinline__ bool produce(const KArgs &a, int lane, int ng, int cnt, int jb, int &k, int &off)
     {
-        if (lane == 0) {
-            const uint32_t st = issued % STAGES;
-            tma_issue(bar(st), smem_addr(tile(st)), a.pos + j, (uint32_t)n * 16u, smem_addr(tile(st) + JT),
-                      is_adjoint(MODE) ? (const void *)(a.lam + j) : nullptr);
+        const uint32_t st = issued % STAGES;
+        float4 *dst = tile(st);
+        int filled = 0;
+        bool fenced = false;
+        while (k < ng && filled < JT) {
+            const int c = __shfl_sync(FULL, cnt, k);
+            if (off >= c) {
+                ++k;
+                off = 0;
+                continue;
+            }
+            const int n = min(JT - filled, c - off);
+            const int src = __shfl_sync(FULL, jb, k) + off;
+            if (lane == 0) {
+                if (!fenced) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    fenced = true;
+                }
+                tma_expect_copy(bar(st), smem_addr(dst + filled), a.pos + src, (uint32_t)n * 16u);
+                if constexpr (NBUF == 2)
+                    tma_expect_copy(bar(st), smem_addr(dst + JT + filled), a.lam + src, (uint32_t)n * 16u);
+            }
+            filled += n;
+            off += n;
         }
+        if (filled == 0) return false;
+        if (lane == 0) mbar_arrive(bar(st));
         ++issued;
+        return true;
     }
     // bounded wait for the next tile; false if the wait ran out
     __device__ __forceinline__ bool wait_next() const
@@ -494,44 +503,49 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
             Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
         }
-        int pk = 0, poff = 0, pn = 0;  // producer cursor
-        int ck = 0, coff = 0, cn = 0;  // consumer cursor
-        for (int s = 0; s < STAGES; ++s) {  // prologue: fill the ring
-            if (!next_tile<JT>(ng, cnt, pk, poff, pn)) break;
-            ring.issue(a, lane, __shfl_sync(FULL, jb, pk) + poff, pn);
-            poff += pn;
-        }
+        int pk = 0, poff = 0;  // producer cursor (entry, record within it)
+        int ck = 0, coff = 0;  // consumer cursor
+        for (int s = 0; s < STAGES; ++s)  // prologue: fill the ring
+            if (!ring.produce(a, lane, ng, cnt, jb, pk, poff)) break;
         int cur = -1;
         float op[IPL][3];
         while (ring.consumed < ring.issued) {
-            next_tile<JT>(ng, cnt, ck, coff, cn);
             if (!ring.wait_next()) return false;
-            if (ck != cur) {
-                cur = ck;
-                const float dx = __shfl_sync(FULL, Dx, ck), dy = __shfl_sync(FULL, Dy, ck),
-                            dz = __shfl_sync(FULL, Dz, ck);
-#pragma unroll
-                for (int u = 0; u < IPL; ++u) {
-                    op[u][0] = oi[u].x - dx;
-                    op[u][1] = oi[u].y - dy;
-                    op[u][2] = oi[u].z - dz;
-                }
-            }
             const float4 *tj = ring.tile(ring.consumed % STAGES);
-            if constexpr (MODE == FORCE)
-                tile_force<IPL>(tj, cn, op, K, A);
-            else if constexpr (MODE == POTENTIAL)
-                tile_potential<IPL>(tj, cn, op, K, A);
-            else
-                tile_adjoint<MODE, IPL>(tj, tj + JT, cn, op, oi, li, K, A);
+            // replay the producer's pieces: each piece is one entry's records
+            int filled = 0;
+            while (ck < ng && filled < JT) {
+                const int c = __shfl_sync(FULL, cnt, ck);
+                if (coff >= c) {
+                    ++ck;
+                    coff = 0;
+                    continue;
+                }
+                const int n = min(JT - filled, c - coff);
+                if (ck != cur) {
+                    cur = ck;
+                    const float dx = __shfl_sync(FULL, Dx, ck), dy = __shfl_sync(FULL, Dy, ck),
+                                dz = __shfl_sync(FULL, Dz, ck);
+#pragma unroll
+                    for (int u = 0; u < IPL; ++u) {
+                        op[u][0] = oi[u].x - dx;
+                        op[u][1] = oi[u].y - dy;
+                        op[u][2] = oi[u].z - dz;
+                    }
+                }
+                if constexpr (MODE == FORCE)
+                    tile_force<IPL>(tj + filled, n, op, K, A);
+                else if constexpr (MODE == POTENTIAL)
+                    tile_potential<IPL>(tj + filled, n, op, K, A);
+                else
+                    tile_adjoint<MODE, IPL>(tj + filled, tj + JT + filled, n, op, oi, li, K, A);
+                filled += n;
+                coff += n;
+            }
             A.fold();
-            coff += cn;
             ++ring.consumed;
             __syncwarp();
-            if (next_tile<JT>(ng, cnt, pk, poff, pn)) {
-                ring.issue(a, lane, __shfl_sync(FULL, jb, pk) + poff, pn);
-                poff += pn;
-            }
+            ring.produce(a, lane, ng, cnt, jb, pk, poff);
         }
     }
 #pragma unroll
@@ -561,8 +575,13 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
 // Persistent work-stealing kernel: each warp takes tasks from a global
 // counter until none is left.  A task of more than 32 particles runs two i
 // particles per lane.
+// Register budgets: the forward and potential kernels keep 80 registers so that
+// 3 CTAs (24 warps) fit an SM; the adjoint's staging needs twice the shared
+// memory, which caps it at 2 CTAs, so it may use up to 128 registers.
+__host__ __device__ constexpr int min_ctas(int mode) { return is_adjoint(mode) ? 2 : 3; }
+
 template <int MODE, int JT, int STAGES>
-__global__ void __launch_bounds__(256, 3) k_pairs(const KArgs a)
+__global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int WARP_BYTES = warp_smem_bytes(MODE, JT, STAGES);

@@ -58,6 +58,12 @@ def configure(L):
     L.ora_lists.argtypes = [ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.ora_lists.restype = ctypes.c_int64
+    L.ora_rcb_build.argtypes = [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32,
+                                ctypes.c_int32, _i32p, _i32p, _i32p, _f32p]
+    L.ora_rcb_build.restype = ctypes.c_int64
+    L.ora_rcb_lists.argtypes = [ctypes.c_int64, _i32p, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.ora_rcb_lists.restype = ctypes.c_int64
     L.ora_tasks.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
     L.ora_tasks.restype = ctypes.c_int64
     L.ora_fsr.argtypes = [ctypes.c_double, ctypes.c_double, _f64p]
@@ -148,6 +154,36 @@ def lists_volume(n: int, w: float, rcut: float):
     shift = np.zeros(cnt, np.int8)
     L_.ora_lists(int(n), float(w), float(rcut), off.ctypes.data, cell.ctypes.data, shift.ctypes.data)
     return off, cell, shift
+
+
+def rcb_volume(x, y, z, m, L: float, leaf_max: int, max_depth: int = 48) -> dict:
+    """Reference RCB fat-leaf tree of one volume (see ora_rcb_build):
+    perm, leaf_start[n_leaves + 1], leaf_qbox[n_leaves, 6] (integer lo xyz,
+    hi xyz on the 2^21 grid), sorted4 (leaf-relative offsets and mass)."""
+    N = int(np.asarray(x).shape[0])
+    perm = np.zeros(max(N, 1), np.int32)
+    leaf_start = np.zeros(N + 2, np.int32)
+    qbox = np.zeros((N + 1) * 6, np.int32)
+    sorted4 = np.zeros((max(N, 1), 4), np.float32)
+    nl = lib().ora_rcb_build(_c32(x), _c32(y), _c32(z), _c32(m), N, float(L), int(leaf_max), int(max_depth), perm,
+                             leaf_start, qbox, sorted4.reshape(-1))
+    assert nl >= 0
+    return dict(n_leaves=int(nl), perm=perm[:N], leaf_start=leaf_start[:nl + 1],
+                leaf_qbox=qbox[:6 * nl].reshape(nl, 6), sorted4=sorted4[:N])
+
+
+def rcb_lists(leaf_qbox: np.ndarray, L: float, rcut: float):
+    """Reference leaf interaction lists (see ora_rcb_lists):
+    (nbr_off int64[n_leaves + 1], nbr_leaf int32, nbr_shift int8)."""
+    q = np.ascontiguousarray(leaf_qbox, dtype=np.int32).reshape(-1)
+    nl = q.shape[0] // 6
+    L_ = lib()
+    cnt = L_.ora_rcb_lists(nl, q, float(L), float(rcut), None, None, None)
+    off = np.zeros(nl + 1, np.int64)
+    leaf = np.zeros(cnt, np.int32)
+    shift = np.zeros(cnt, np.int8)
+    L_.ora_rcb_lists(nl, q, float(L), float(rcut), off.ctypes.data, leaf.ctypes.data, shift.ctypes.data)
+    return off, leaf, shift
 
 
 def reach(w: float, rcut: float) -> int:

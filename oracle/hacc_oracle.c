@@ -245,6 +245,199 @@ int64_t ora_tasks(const int32_t *cell_start, int64_t ncells, int32_t T, int32_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Recursive coordinate bisection (RCB) tree with fat leaves                 */
+/* ------------------------------------------------------------------------ */
+
+/* The paper's short-range tree (Sec. III, spatial locality): divide a group
+ * of particles in two at the centre of mass along the longest side of its
+ * box, keep each half in its own contiguous range, recurse until a leaf holds
+ * at most leaf_max particles.  Exact integer version of that rule, so the
+ * tree is reproducible bit for bit: per axis q = floor(xw 2^21 / L) in
+ * [0, 2^21) (xw the float32-wrapped coordinate, the product in float64); the
+ * box is the integer min/max of q; the split axis is the longest side (lowest
+ * axis on ties); the split value is the floor of the integer mean of q (the
+ * centre of mass of equal-mass particles); a particle goes left iff
+ * q <= split; the partition is stable.  If every side has length 0 the first
+ * half (cnt / 2 particles, by position) goes left.  A group becomes a leaf
+ * when it holds at most leaf_max particles or sits at depth max_depth (the
+ * roots have depth 0).  Leaves come out in depth-first, left-first order,
+ * which is the order of their first slots. */
+#define ORA_QBITS 21
+
+static int32_t quant21(float xw, float L)
+{
+    double t = (double)xw * ((double)(1 << ORA_QBITS) / (double)L);
+    int64_t q = (int64_t)floor(t);
+    if (q > (1 << ORA_QBITS) - 1) q = (1 << ORA_QBITS) - 1;
+    if (q < 0) q = 0;
+    return (int32_t)q;
+}
+
+typedef struct {
+    int32_t *q;    /* [3 N] quantised coordinates in current order */
+    int32_t *idx;  /* [N] original index in current order */
+    int32_t *tmp;  /* [4 N] scratch */
+    int32_t leaf_max;
+    int32_t max_depth;
+    int64_t n_leaves;
+    int32_t *leaf_start; /* appended */
+    int32_t *leaf_qbox;  /* appended: 6 per leaf (lo xyz, hi xyz) */
+} ora_rcb_state;
+
+static void rcb_split(ora_rcb_state *S, int64_t b, int64_t e, int32_t depth)
+{
+    int64_t cnt = e - b;
+    if (cnt <= 0) return; /* never reached by the rule above (both halves are non-empty) */
+    int32_t lo[3], hi[3];
+    int64_t sum[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = S->q[3 * b + a];
+        hi[a] = S->q[3 * b + a];
+    }
+    for (int64_t i = b; i < e; ++i)
+        for (int a = 0; a < 3; ++a) {
+            int32_t v = S->q[3 * i + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+            sum[a] += v;
+        }
+    if (cnt <= S->leaf_max || depth >= S->max_depth) {
+        int64_t l = S->n_leaves++;
+        S->leaf_start[l] = (int32_t)b;
+        for (int a = 0; a < 3; ++a) {
+            S->leaf_qbox[6 * l + a] = lo[a];
+            S->leaf_qbox[6 * l + 3 + a] = hi[a];
+        }
+        return;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+        if (hi[a] - lo[a] > hi[axis] - lo[axis]) axis = a;
+    int64_t nl = 0;
+    if (hi[axis] == lo[axis]) {
+        nl = cnt / 2; /* coincident: split by position */
+    } else {
+        int64_t split = sum[axis] / cnt; /* floor of the mean (non-negative) */
+        /* stable partition through the scratch array */
+        int64_t w = 0;
+        for (int64_t pass = 0; pass < 2; ++pass)
+            for (int64_t i = b; i < e; ++i) {
+                int left = S->q[3 * i + axis] <= split;
+                if ((pass == 0) == (left != 0)) {
+                    for (int a = 0; a < 3; ++a) S->tmp[4 * w + a] = S->q[3 * i + a];
+                    S->tmp[4 * w + 3] = S->idx[i];
+                    ++w;
+                    if (pass == 0) ++nl;
+                }
+            }
+        for (int64_t k = 0; k < cnt; ++k) {
+            for (int a = 0; a < 3; ++a) S->q[3 * (b + k) + a] = S->tmp[4 * k + a];
+            S->idx[b + k] = S->tmp[4 * k + 3];
+        }
+    }
+    rcb_split(S, b, b + nl, depth + 1);
+    rcb_split(S, b + nl, e, depth + 1);
+}
+
+/* RCB of one volume.  Outputs (capacity N + 1 leaves): perm[k] = original
+ * index at tree slot k; leaf_start[0..n_leaves] (leaf_start[n_leaves] = N);
+ * leaf_qbox[6 l..6 l + 5] the leaf's integer box; sorted4 = (o, m) with
+ * o = xw - origin rounded once to float32 (float64 difference), origin =
+ * float32 of qlo L / 2^21 (the leaf's conservative lower corner).  Returns the
+ * number of leaves, or -1 on allocation failure. */
+int64_t ora_rcb_build(const float *x, const float *y, const float *z, const float *m, int64_t N, float L,
+                      int32_t leaf_max, int32_t max_depth, int32_t *perm, int32_t *leaf_start, int32_t *leaf_qbox, float *sorted4)
+{
+    ora_rcb_state S;
+    S.q = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * 3 * sizeof(int32_t));
+    S.idx = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
+    S.tmp = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * 4 * sizeof(int32_t));
+    if (!S.q || !S.idx || !S.tmp) {
+        free(S.q);
+        free(S.idx);
+        free(S.tmp);
+        return -1;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        S.q[3 * i + 0] = quant21(wrap32(x[i], L), L);
+        S.q[3 * i + 1] = quant21(wrap32(y[i], L), L);
+        S.q[3 * i + 2] = quant21(wrap32(z[i], L), L);
+        S.idx[i] = (int32_t)i;
+    }
+    S.leaf_max = leaf_max;
+    S.max_depth = max_depth;
+    S.n_leaves = 0;
+    S.leaf_start = leaf_start;
+    S.leaf_qbox = leaf_qbox;
+    if (N > 0) rcb_split(&S, 0, N, 0);
+    leaf_start[S.n_leaves] = (int32_t)N;
+    double scale = (double)L / (double)(1 << ORA_QBITS);
+    for (int64_t l = 0; l < S.n_leaves; ++l) {
+        float org[3];
+        for (int a = 0; a < 3; ++a) org[a] = (float)((double)leaf_qbox[6 * l + a] * scale);
+        for (int64_t k = leaf_start[l]; k < leaf_start[l + 1]; ++k) {
+            int32_t i = S.idx[k];
+            perm[k] = i;
+            sorted4[4 * k + 0] = (float)((double)wrap32(x[i], L) - (double)org[0]);
+            sorted4[4 * k + 1] = (float)((double)wrap32(y[i], L) - (double)org[1]);
+            sorted4[4 * k + 2] = (float)((double)wrap32(z[i], L) - (double)org[2]);
+            sorted4[4 * k + 3] = m[i];
+        }
+    }
+    free(S.q);
+    free(S.idx);
+    free(S.tmp);
+    return S.n_leaves;
+}
+
+/* Leaf interaction lists of one volume (the tree walk's result, by brute
+ * force over leaf pairs): leaf j with image shift s is listed for leaf i iff
+ * their boxes come closer than r_c:
+ *   sum_a max(0, lo_j,a + s_a L - hi_i,a, lo_i,a - hi_j,a - s_a L)^2 < r_c^2
+ * in float64, each leaf box widened by one grid quantum q_L = L / 2^21 on
+ * every side, [(qlo - 1) q_L, (qhi + 2) q_L], so that it holds its particles
+ * whatever the rounding of the quantisation.  Canonical order per i:
+ * ascending shift code (sz+1)*9 + (sy+1)*3 + (sx+1), then ascending j.
+ * nbr_off[n_leaves + 1]; entries (j, code) when nbr_leaf != NULL.  Returns
+ * the entry count. */
+int64_t ora_rcb_lists(int64_t n_leaves, const int32_t *leaf_qbox, float L, float rcut, int64_t *nbr_off,
+                      int32_t *nbr_leaf, int8_t *nbr_shift)
+{
+    double scale = (double)L / (double)(1 << ORA_QBITS);
+    double rc2 = (double)rcut * (double)rcut;
+    int64_t e = 0;
+    for (int64_t i = 0; i < n_leaves; ++i) {
+        if (nbr_off) nbr_off[i] = e;
+        for (int code = 0; code < 27; ++code) {
+            int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+            int sh[3] = {sx, sy, sz};
+            for (int64_t j = 0; j < n_leaves; ++j) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double ilo = (double)(leaf_qbox[6 * i + a] - 1) * scale;
+                    double ihi = (double)(leaf_qbox[6 * i + 3 + a] + 2) * scale;
+                    double jlo = (double)(leaf_qbox[6 * j + a] - 1) * scale + (double)sh[a] * (double)L;
+                    double jhi = (double)(leaf_qbox[6 * j + 3 + a] + 2) * scale + (double)sh[a] * (double)L;
+                    double g = 0.0;
+                    if (jlo - ihi > g) g = jlo - ihi;
+                    if (ilo - jhi > g) g = ilo - jhi;
+                    d2 += g * g;
+                }
+                if (d2 < rc2) {
+                    if (nbr_leaf) {
+                        nbr_leaf[e] = (int32_t)j;
+                        nbr_shift[e] = (int8_t)code;
+                    }
+                    ++e;
+                }
+            }
+        }
+    }
+    if (nbr_off) nbr_off[n_leaves] = e;
+    return e;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Short-range force (Eq. 7), brute force in float64                         */
 /* ------------------------------------------------------------------------ */
 

@@ -43,6 +43,15 @@ MUTANTS = [
     ("potential sign", "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) + 0.5 * P6(c, s));",
      "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) - 0.5 * P6(c, s));"),
     ("potential polynomial index", "s * (c[4] / 5.0 + s * c[5] / 6.0)", "s * (c[4] / 5.0 + s * c[5] / 5.0)"),
+    ("rcb axis: shortest side", "if (hi[a] - lo[a] > hi[axis] - lo[axis]) axis = a;",
+     "if (hi[a] - lo[a] < hi[axis] - lo[axis]) axis = a;"),
+    ("rcb strict split", "int left = S->q[3 * i + axis] <= split;", "int left = S->q[3 * i + axis] < split;"),
+    ("rcb mean rounded up", "int64_t split = sum[axis] / cnt;", "int64_t split = (sum[axis] + cnt - 1) / cnt;"),
+    ("rcb unstable partition", "for (int64_t i = b; i < e; ++i) {\n                int left",
+     "for (int64_t i = e - 1; i >= b; --i) {\n                int left"),
+    ("rcb leaf size off by one", "if (cnt <= S->leaf_max || depth", "if (cnt < S->leaf_max || depth"),
+    ("rcb image shift sign", "double jlo = (double)(leaf_qbox[6 * j + a] - 1) * scale + (double)sh[a] * (double)L;",
+     "double jlo = (double)(leaf_qbox[6 * j + a] - 1) * scale - (double)sh[a] * (double)L;"),
     ("drift before kick", "        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += dt_d * vx[i];",
      "        if (x) x[i] += dt_d * vx[i];\n        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += 0.0;"),
 ]
@@ -66,6 +75,11 @@ PINS = [
     pins.test_binning_invariants_and_numpy_restatement,
     pins.test_binning_with_displacements_keeps_float64_positions,
     lambda: pins.test_lists_cover_every_pair_within_cutoff(16.0, 3.0, 3.0),
+    pins.test_rcb_hand_worked_examples,
+    pins.test_rcb_regular_lattice_is_bit_interleaved,
+    pins.test_rcb_leaves_invariants_on_clustered_particles,
+    lambda: pins.test_rcb_lists_cover_every_pair_within_cutoff("uniform", 16),
+    lambda: pins.test_rcb_lists_cover_every_pair_within_cutoff("clustered", 24),
     pins.test_trajectory_gradient_against_finite_differences,
 ]
 

@@ -452,6 +452,137 @@ def test_tasks_partition_each_cell():
 
 
 # --------------------------------------------------------------------------
+# RCB fat-leaf tree (Sec. III) and its leaf lists
+# --------------------------------------------------------------------------
+
+def test_rcb_hand_worked_examples():
+    """Small trees worked out by hand from the rule (centre-of-mass split
+    along the longest side, left iff q <= floor(mean q), stable halves).
+    L = 64: q = 32768 x exactly for these positions."""
+    one = np.ones(6, np.float32)
+    x = np.array([1, 9, 2, 8, 3, 10], np.float32)
+    y = np.array([0, 0, 0, 1, 0, 0], np.float32)
+    z = np.zeros(6, np.float32)
+    # root: x spans 9, mean 5.5 -> {0, 2, 4} | {1, 3, 5}; left: mean 2 -> {0, 2} | {4} (x = 2 goes
+    # left: q <= split); right: x spans 2 > y's 1, mean 9 -> {1, 3} | {5}
+    r = oracle.rcb_volume(x, y, z, one, 64.0, 2)
+    assert r["perm"].tolist() == [0, 2, 4, 1, 3, 5]
+    assert r["leaf_start"].tolist() == [0, 2, 3, 5, 6]
+    assert (r["leaf_qbox"] // 32768).tolist() == [[1, 0, 0, 2, 0, 0], [3, 0, 0, 3, 0, 0],
+                                                  [8, 0, 0, 9, 1, 0], [10, 0, 0, 10, 0, 0]]
+    # depth cap 1: only the root splits
+    r = oracle.rcb_volume(x, y, z, one, 64.0, 2, max_depth=1)
+    assert r["leaf_start"].tolist() == [0, 3, 6]
+    # the longest side decides the axis: y spans 6 > x's 2
+    x2 = np.array([1, 2, 3, 1, 2, 3], np.float32)
+    y2 = np.array([0, 6, 1, 5, 2, 4], np.float32)
+    r = oracle.rcb_volume(x2, y2, z, one, 64.0, 3)
+    assert r["perm"].tolist() == [0, 2, 4, 1, 3, 5]  # mean y 3: {0, 2, 4} (y 0, 1, 2) | {1, 3, 5}
+    # a mean between grid points is floored: q = q0 + (0, 1, 1) has mean q0 + 2/3, so only the
+    # first particle goes left (rounding up would keep all three together)
+    u = np.float32(1.0 / 32768)
+    x3 = np.array([10.0, 10.0 + u, 10.0 + u], np.float32)
+    r = oracle.rcb_volume(x3, z[:3], z[:3], one[:3], 64.0, 1)
+    assert r["leaf_start"].tolist() == [0, 1, 2, 3]
+    # coincident particles: halves by position, cnt / 2 to the left
+    c3 = np.full(3, 7.0, np.float32)
+    r = oracle.rcb_volume(c3, c3, c3, one[:3], 64.0, 1)
+    assert r["perm"].tolist() == [0, 1, 2] and r["leaf_start"].tolist() == [0, 1, 2, 3]
+
+
+def test_rcb_regular_lattice_is_bit_interleaved():
+    """On a 4^3 lattice every centre of mass is a midpoint, so each split halves
+    the group and the axis cycles x, y, z (ties go to the lowest axis): the
+    leaf order is the bit-interleaved (Morton) order with x most significant."""
+    L = 16.0
+    g = np.arange(4)
+    ix, iy, iz = [a.reshape(-1) for a in np.meshgrid(g, g, g, indexing="ij")]
+    order = np.random.default_rng(5).permutation(64)
+    ix, iy, iz = ix[order], iy[order], iz[order]
+    x, y, z = [(4 * a + 1).astype(np.float32) for a in (ix, iy, iz)]
+    m = np.ones(64, np.float32)
+    key = lambda a, b, c: (a >> 1) * 32 + (b >> 1) * 16 + (c >> 1) * 8 + (a & 1) * 4 + (b & 1) * 2 + (c & 1)
+    k = key(ix, iy, iz)
+    r = oracle.rcb_volume(x, y, z, m, L, 1)
+    assert r["n_leaves"] == 64 and np.array_equal(k[r["perm"]], np.arange(64))
+    r = oracle.rcb_volume(x, y, z, m, L, 8)
+    assert r["leaf_start"].tolist() == list(range(0, 65, 8))
+    octant = k[r["perm"]] // 8
+    assert np.array_equal(octant, np.repeat(np.arange(8), 8))
+    for l in range(8):  # stable: input order within each leaf
+        assert np.all(np.diff(r["perm"][8 * l:8 * l + 8]) > 0)
+
+
+def _quant21_numpy(xw, L):
+    return np.minimum(np.floor(xw.astype(np.float64) * (2.0 ** 21 / np.float64(L))), 2 ** 21 - 1).astype(np.int64)
+
+
+def test_rcb_leaves_invariants_on_clustered_particles():
+    from synth.workloads import clustered_box
+    w = clustered_box(24, 3, seed=17)
+    L = float(w.L[0])
+    for leaf_max in (1, 7, 32, 64):
+        r = oracle.rcb_volume(w.x, w.y, w.z, w.m, L, leaf_max)
+        perm, ls, qb, s4 = r["perm"], r["leaf_start"], r["leaf_qbox"], r["sorted4"]
+        assert np.array_equal(np.sort(perm), np.arange(w.N))
+        sizes = np.diff(ls)
+        assert ls[0] == 0 and ls[-1] == w.N and np.all(sizes >= 1) and np.all(sizes <= leaf_max)
+        xw = [_wrap_f32_numpy(a, L) for a in (w.x, w.y, w.z)]
+        q = np.stack([_quant21_numpy(a, L) for a in xw], 1)
+        scale = L / 2.0 ** 21
+        for l in range(r["n_leaves"]):
+            idx = perm[ls[l]:ls[l + 1]]
+            assert np.all(np.diff(idx) > 0)  # stable partitions keep input order
+            assert np.array_equal(qb[l, :3], q[idx].min(0)) and np.array_equal(qb[l, 3:], q[idx].max(0))
+            org = (qb[l, :3] * scale).astype(np.float32).astype(np.float64)
+            for a in range(3):
+                pos = s4[ls[l]:ls[l + 1], a].astype(np.float64) + org[a]
+                assert np.max(np.abs(pos - xw[a][idx])) <= 2 * np.spacing(np.float32(L))
+        assert np.array_equal(s4[:, 3], w.m[perm])
+    # a group of more than leaf_max particles always splits in two non-empty halves,
+    # so the leaves of one size bound nest in those of a larger one
+    big = oracle.rcb_volume(w.x, w.y, w.z, w.m, L, 64)
+    small = oracle.rcb_volume(w.x, w.y, w.z, w.m, L, 32)
+    assert set(big["leaf_start"].tolist()) <= set(small["leaf_start"].tolist())
+    for b, e in zip(big["leaf_start"][:-1], big["leaf_start"][1:]):
+        assert np.array_equal(np.sort(big["perm"][b:e]), np.sort(small["perm"][b:e]))
+
+
+@pytest.mark.parametrize("maker,leaf_max", [("uniform", 16), ("clustered", 24)])
+def test_rcb_lists_cover_every_pair_within_cutoff(maker, leaf_max):
+    """Brute force: every pair closer than r_c sits in a listed (leaf, leaf,
+    image); the lists are symmetric, hold each leaf itself, and are in
+    canonical order."""
+    from synth.workloads import clustered_box
+    w = uniform_box(1200, 12.0, seed=8) if maker == "uniform" else clustered_box(16, 2, seed=9)
+    L = float(w.L[0])
+    r = oracle.rcb_volume(w.x, w.y, w.z, w.m, L, leaf_max)
+    off, leaf, shift = oracle.rcb_lists(r["leaf_qbox"], L, RC)
+    nl = r["n_leaves"]
+    listed = set()
+    for i in range(nl):
+        ent = list(zip(shift[off[i]:off[i + 1]].tolist(), leaf[off[i]:off[i + 1]].tolist()))
+        assert ent == sorted(ent) and len(set(ent)) == len(ent)
+        assert (13, i) in ent
+        listed.update((i, j, c) for c, j in ent)
+    assert all((j, i, 26 - c) in listed for i, j, c in listed)
+    leaf_of = np.zeros(w.N, np.int64)
+    for l in range(nl):
+        leaf_of[r["perm"][r["leaf_start"][l]:r["leaf_start"][l + 1]]] = l
+    p = np.stack([_wrap_f32_numpy(a, L) for a in (w.x, w.y, w.z)], 1).astype(np.float64)
+    d = p[None] - p[:, None]          # d[i, j] = x_j - x_i
+    img = -np.round(d / L)            # image s of j that lies next to i
+    dd = d + L * img
+    close = ((dd * dd).sum(-1) < RC * RC) & ~np.eye(w.N, dtype=bool)
+    ii, jj = np.nonzero(close)
+    sh = img[ii, jj].astype(int)
+    code = (sh[:, 2] + 1) * 9 + (sh[:, 1] + 1) * 3 + (sh[:, 0] + 1)
+    missing = [(a, b, c) for a, b, c in zip(leaf_of[ii], leaf_of[jj], code) if (a, b, c) not in listed]
+    assert not missing, missing[:5]
+    assert len(ii) > 1000
+
+
+# --------------------------------------------------------------------------
 # grid-force fit (input generator of the coefficients)
 # --------------------------------------------------------------------------
 

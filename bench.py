@@ -65,6 +65,8 @@ def parse():
                     help="replay the step as one captured CUDA graph (auto: on for batched256)")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     ap.add_argument("--no-sks", action="store_true", help="skip the sub-cycle (SKS) measurement")
+    ap.add_argument("--no-tree", action="store_true", help="skip the RCB tree vs chaining mesh comparison")
+    ap.add_argument("--leaf-max", type=int, default=64, help="RCB leaf size bound of the tree comparison")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the step: force-kernel rate vs neighbour-list length and occupancy")
     return ap.parse_args()
@@ -323,6 +325,11 @@ def run_ours(args):
     if not args.no_diff and ranks.rank == 0:
         out["differentiation"] = differentiation(torch, hs)
 
+    # the paper's RCB fat-leaf tree as the list builder, against the chaining mesh
+    if not args.no_tree and ranks.rank == 0 and w.V == 1:
+        out["tree_vs_mesh"] = tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs, within,
+                                           args.leaf_max)
+
     # short-range sub-cycles of the split-operator step: throughput and drift
     if not args.no_sks and ranks.rank == 0:
         out["sks"] = sks_measure(torch, hs)
@@ -398,6 +405,60 @@ def force_traffic(config: str):
     if config != FORCE_TRAFFIC["workload"] or sha != FORCE_TRAFFIC["source_sha256"]:
         return None
     return FORCE_TRAFFIC["bytes"]
+
+
+def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs, within, leaf_max, reps=3):
+    """Same positions, same pair kernel, lists from the RCB fat-leaf tree
+    (Sec. III) instead of the chaining mesh: build, walk and force times,
+    candidate and within-cutoff pairs, and the force difference between the
+    two (float32 rounding only: both visit every pair inside the cutoff)."""
+    tr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=split_T, builder="rcb", leaf_max=leaf_max)
+    tr.prepare(pos, m)
+    a_t = tr.force(prm, launch=launch)
+    torch.cuda.synchronize()
+    tr.check_status()
+    tb = []
+    for _ in range(reps):  # the build synchronises once per level: host clock around it
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs.hacc_rcb_build(tr.mesh, pos[0], pos[1], pos[2], m, tr.tree, tr.binned, tr.ws, tr.status)
+        torch.cuda.synchronize()
+        tb.append((time.perf_counter() - t0) * 1e3)
+
+    def ev(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_lists = ev(lambda: hs.hacc_rcb_lists(tr.mesh, tr.tree, tr.lists, tr.entry_cap, tr.n_entries_dev, tr.ws,
+                                           tr.status))
+    t_tforce = ev(lambda: tr.force(prm, a_t, launch=launch))
+    t_prep = ev(lambda: sr.prepare(pos, m))
+    a_m = sr.force(prm, launch=launch)
+    torch.cuda.synchronize()
+    tr.check_status()
+    sr.check_status()
+    rel = float((a_t.double() - a_m.double()).norm() / a_m.double().norm())
+    t_pairs = tr.pair_count()
+    t_within = tr.pairs_within_cutoff(prm)
+    res = {"leaf_max": leaf_max, "n_leaves": int(tr.n_leaves.item()), "n_nodes": int(tr.n_nodes.item()),
+           "leaf_list_entries": tr.n_entries,
+           "tree": {"build_ms": min(tb), "lists_ms": t_lists, "force_ms": t_tforce, "candidate_pairs": t_pairs,
+                    "pairs_within_cutoff": t_within, "list_efficiency": t_within / t_pairs,
+                    "pairs_per_s": t_pairs / (t_tforce * 1e-3),
+                    "within_cutoff_pairs_per_s": t_within / (t_tforce * 1e-3)},
+           "mesh": {"bin_plus_lists_ms": t_prep, "force_ms": t_force, "candidate_pairs": pairs,
+                    "pairs_within_cutoff": within, "list_efficiency": within / pairs,
+                    "pairs_per_s": pairs / (t_force * 1e-3),
+                    "within_cutoff_pairs_per_s": within / (t_force * 1e-3)},
+           "force_rel_diff_tree_vs_mesh": rel}
+    del tr
+    torch.cuda.empty_cache()
+    return res
 
 
 def sks_measure(torch, hs, n_c: int = 10, h: float = 0.01):

@@ -84,12 +84,16 @@ typedef struct hacc_mesh {
     int64_t n_entries; /* neighbour-list entries over all volumes */
 } hacc_mesh;
 
-/* Output of hacc_bin. */
+/* Output of hacc_bin (chaining-mesh cells) or of hacc_rcb_build (tree
+ * leaves, which then play the cells: cell_start = the tree's leaf_start,
+ * cell_origin = its leaf_origin). */
 typedef struct hacc_binned {
-    int32_t *cell_of;    /* [N] global cell of particle i (input order) */
+    int32_t *cell_of;    /* [N] global cell (leaf) of particle i (input order); may be NULL for the tree */
     int32_t *cell_start; /* [n_cells + 1] first sorted slot of each cell */
     int32_t *perm;       /* [N] input index of the particle in sorted slot k */
     float *sorted4;      /* [4 N] per sorted slot (ox, oy, oz, m), o = cell-relative offset */
+    float *cell_origin;  /* [4 n_cells] (x, y, z, 0) origin the offsets of each cell are taken from,
+                            or NULL for the chaining mesh (cell (cx, cy, cz) sits at float32 c w) */
 } hacc_binned;
 
 /* Output of hacc_build_lists. */
@@ -206,6 +210,75 @@ size_t hacc_lists_workspace_size(const hacc_mesh *mesh);
  * sets HACC_STATUS_CAPACITY (the surplus is not written). */
 int hacc_build_lists(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
                      void *ws, size_t ws_bytes, uint32_t *status, void *stream);
+
+/* ---- RCB fat-leaf tree: the paper's own list builder (Sec. III) ---------
+ * An alternative to hacc_bin + hacc_build_lists whose leaves take the place
+ * of the chaining-mesh cells; the pair calls (hacc_sr_force, the adjoint, the
+ * potential, hacc_count_pairs) take its output unchanged. */
+#define HACC_RCB_QBITS 21     /* quantisation: 2^21 steps per box side */
+#define HACC_RCB_MAX_DEPTH 64 /* largest accepted max_depth */
+
+typedef struct hacc_tree {
+    int32_t leaf_max;    /* in: a group of more than leaf_max particles is split, >= 1 */
+    int32_t max_depth;   /* in: groups at this depth become leaves whatever their size,
+                            0..HACC_RCB_MAX_DEPTH (roots have depth 0) */
+    int64_t leaf_cap;    /* in: capacity of the leaf and node arrays, in leaves (N suffices) */
+    int32_t *n_leaves;   /* device scalar out */
+    int32_t *n_nodes;    /* device scalar out: internal nodes */
+    int32_t *leaf_start; /* [leaf_cap + 1] first sorted slot of each leaf, [n_leaves] = N */
+    int32_t *leaf_qbox;  /* [6 leaf_cap] leaf box on the 2^21 grid of its volume: lo xyz, hi xyz */
+    float *leaf_origin;  /* [4 leaf_cap] (x, y, z, 0): float32 of lo L / 2^21 (float64 product) */
+    int32_t *node_qbox;  /* [6 leaf_cap] boxes of the internal nodes, same layout */
+    int32_t *node_child; /* [2 leaf_cap] left, right child: node id >= 0, or -1 - leaf id */
+    int32_t *root;       /* [V] root of each volume: node id, -1 - leaf id, or INT32_MIN if empty */
+} hacc_tree;
+
+/* Bytes of scratch that hacc_rcb_build needs for groups of more than leaf_max
+ * particles. */
+size_t hacc_rcb_build_workspace_size(const hacc_mesh *mesh, int32_t leaf_max);
+
+/* Recursive coordinate bisection of every volume into leaves of at most
+ * leaf_max particles (Sec. III: split at the centre of mass, perpendicular
+ * to the longest side of the group's box, halves kept contiguous), made exact
+ * in integers so the tree is reproducible bit for bit.  Per axis q =
+ * floor(xw 2^21 / L), clamped to [0, 2^21), xw wrapped as in hacc_bin, the
+ * product in float64; the box of a group is the min/max of its q; the split
+ * axis is the longest side (lowest axis on ties), the split value the floor
+ * of the mean q (equal masses: the centre of mass); a particle goes left iff
+ * q <= split, the partition is stable; a group whose box is a point is
+ * halved by position (cnt/2 left).  Leaves are numbered depth first, left
+ * first (= by first slot).  Writes every array of `tree`, and of `out`:
+ * perm, sorted4 with o = fl32(xw - origin) (float64 difference), cell_of if
+ * not NULL; `out->cell_start` and `out->cell_origin` are not touched (point
+ * them at tree->leaf_start and tree->leaf_origin for the pair calls).
+ * Level-synchronous on the GPU: it SYNCHRONISES `stream` once per tree level
+ * to read the number of groups left, so it cannot be captured in a CUDA
+ * graph.  More leaves or nodes than leaf_cap sets HACC_STATUS_CAPACITY; a
+ * non-finite coordinate sets HACC_STATUS_NONFINITE and is taken as 0. */
+int hacc_rcb_build(const hacc_mesh *mesh, const float *x, const float *y, const float *z, const float *m,
+                   const hacc_tree *tree, const hacc_binned *out, void *ws, size_t ws_bytes, uint32_t *status,
+                   void *stream);
+
+/* Bytes of scratch that hacc_rcb_lists needs. */
+size_t hacc_rcb_lists_workspace_size(const hacc_mesh *mesh, int64_t leaf_cap, int64_t task_cap);
+
+/* Leaf-shared interaction lists by a walk of the tree (Sec. III, walk
+ * minimisation), and the tasks.  Leaf j with periodic image s is listed for
+ * leaf i iff the two leaf boxes, each widened by one grid step L / 2^21 on
+ * every side ([(lo - 1) L / 2^21, (hi + 2) L / 2^21], float64), come closer
+ * than the volume's rcut (sum of squared gaps < rcut^2, float64); entries in
+ * ascending image code (sz+1)*9 + (sy+1)*3 + (sx+1), then ascending j.  An
+ * internal node is skipped when its widened box fails the same test, which
+ * never drops a leaf that passes.  Writes lists->nbr_off [leaf_cap + 1] and
+ * the entry count into the device int64 *n_entries; if lists->nbr_cell is
+ * NULL nothing else is done (a sizing pass).  Otherwise, when the count fits
+ * entry_cap, the entries, and then the tasks (each leaf cut into chunks of at
+ * most split_T particles), task_order (heaviest first, as hacc_build_lists)
+ * and *n_pairs; a count above entry_cap, or more tasks than task_cap, sets
+ * HACC_STATUS_CAPACITY.  Requires a tree built by hacc_rcb_build on the same
+ * mesh. */
+int hacc_rcb_lists(const hacc_mesh *mesh, const hacc_tree *tree, const hacc_lists *lists, int64_t entry_cap,
+                   int64_t *n_entries, void *ws, size_t ws_bytes, uint32_t *status, void *stream);
 
 /* Bytes of scratch that hacc_sr_force / hacc_sr_force_adjoint need. */
 size_t hacc_force_workspace_size(const hacc_mesh *mesh);

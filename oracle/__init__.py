@@ -61,8 +61,8 @@ def configure(L):
     L.ora_rcb_build.argtypes = [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int32,
                                 ctypes.c_int32, _i32p, _i32p, _i32p, _f32p]
     L.ora_rcb_build.restype = ctypes.c_int64
-    L.ora_rcb_lists.argtypes = [ctypes.c_int64, _i32p, ctypes.c_float, ctypes.c_float,
-                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.ora_rcb_lists.argtypes = [ctypes.c_int64, _i32p, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.ora_rcb_lists.restype = ctypes.c_int64
     L.ora_tasks.argtypes = [_i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]
     L.ora_tasks.restype = ctypes.c_int64
@@ -172,18 +172,23 @@ def rcb_volume(x, y, z, m, L: float, leaf_max: int, max_depth: int = 48) -> dict
                 leaf_qbox=qbox[:6 * nl].reshape(nl, 6), sorted4=sorted4[:N])
 
 
-def rcb_lists(leaf_qbox: np.ndarray, L: float, rcut: float):
-    """Reference leaf interaction lists (see ora_rcb_lists):
-    (nbr_off int64[n_leaves + 1], nbr_leaf int32, nbr_shift int8)."""
+def rcb_lists(leaf_qbox: np.ndarray, L: float, rcut: float, targets=None):
+    """Reference leaf interaction lists (see ora_rcb_lists) of every leaf, or of
+    the leaves `targets`: (nbr_off int64[count + 1], nbr_leaf int32, nbr_shift int8)."""
     q = np.ascontiguousarray(leaf_qbox, dtype=np.int32).reshape(-1)
     nl = q.shape[0] // 6
     L_ = lib()
-    cnt = L_.ora_rcb_lists(nl, q, float(L), float(rcut), None, None, None)
-    off = np.zeros(nl + 1, np.int64)
-    leaf = np.zeros(cnt, np.int32)
-    shift = np.zeros(cnt, np.int8)
-    L_.ora_rcb_lists(nl, q, float(L), float(rcut), off.ctypes.data, leaf.ctypes.data, shift.ctypes.data)
-    return off, leaf, shift
+    if targets is None:
+        tp, nt = None, nl
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int64)
+        tp, nt = tg.ctypes.data, tg.shape[0]
+    cnt = L_.ora_rcb_lists(nl, q, float(L), float(rcut), tp, nt, None, None, None)
+    off = np.zeros(nt + 1, np.int64)
+    leaf = np.zeros(max(cnt, 1), np.int32)
+    shift = np.zeros(max(cnt, 1), np.int8)
+    L_.ora_rcb_lists(nl, q, float(L), float(rcut), tp, nt, off.ctypes.data, leaf.ctypes.data, shift.ctypes.data)
+    return off, leaf[:cnt], shift[:cnt]
 
 
 def reach(w: float, rcut: float) -> int:

@@ -398,16 +398,18 @@ int64_t ora_rcb_build(const float *x, const float *y, const float *z, const floa
  * every side, [(qlo - 1) q_L, (qhi + 2) q_L], so that it holds its particles
  * whatever the rounding of the quantisation.  Canonical order per i:
  * ascending shift code (sz+1)*9 + (sy+1)*3 + (sx+1), then ascending j.
- * nbr_off[n_leaves + 1]; entries (j, code) when nbr_leaf != NULL.  Returns
- * the entry count. */
-int64_t ora_rcb_lists(int64_t n_leaves, const int32_t *leaf_qbox, float L, float rcut, int64_t *nbr_off,
-                      int32_t *nbr_leaf, int8_t *nbr_shift)
+ * For the leaves `targets` (NULL: every leaf), nbr_off[count + 1]; entries
+ * (j, code) when nbr_leaf != NULL.  Returns the entry count. */
+int64_t ora_rcb_lists(int64_t n_leaves, const int32_t *leaf_qbox, float L, float rcut, const int64_t *targets,
+                      int64_t n_targets, int64_t *nbr_off, int32_t *nbr_leaf, int8_t *nbr_shift)
 {
     double scale = (double)L / (double)(1 << ORA_QBITS);
     double rc2 = (double)rcut * (double)rcut;
     int64_t e = 0;
-    for (int64_t i = 0; i < n_leaves; ++i) {
-        if (nbr_off) nbr_off[i] = e;
+    int64_t n_i = targets ? n_targets : n_leaves;
+    for (int64_t t = 0; t < n_i; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        if (nbr_off) nbr_off[t] = e;
         for (int code = 0; code < 27; ++code) {
             int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
             int sh[3] = {sx, sy, sz};
@@ -433,7 +435,7 @@ int64_t ora_rcb_lists(int64_t n_leaves, const int32_t *leaf_qbox, float L, float
             }
         }
     }
-    if (nbr_off) nbr_off[n_leaves] = e;
+    if (nbr_off) nbr_off[n_i] = e;
     return e;
 }
 

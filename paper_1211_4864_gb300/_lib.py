@@ -43,13 +43,20 @@ class hacc_mesh(ctypes.Structure):
 
 class hacc_binned(ctypes.Structure):
     _fields_ = [("cell_of", ctypes.c_void_p), ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
-                ("sorted4", ctypes.c_void_p)]
+                ("sorted4", ctypes.c_void_p), ("cell_origin", ctypes.c_void_p)]
 
 
 class hacc_lists(ctypes.Structure):
     _fields_ = [("nbr_off", ctypes.c_void_p), ("nbr_cell", ctypes.c_void_p), ("nbr_shift", ctypes.c_void_p),
                 ("tasks", ctypes.c_void_p), ("n_tasks", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p),
                 ("task_order", ctypes.c_void_p), ("task_cap", ctypes.c_int64), ("split_T", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class hacc_tree(ctypes.Structure):
+    _fields_ = [("leaf_max", ctypes.c_int32), ("max_depth", ctypes.c_int32), ("leaf_cap", ctypes.c_int64),
+                ("n_leaves", ctypes.c_void_p), ("n_nodes", ctypes.c_void_p), ("leaf_start", ctypes.c_void_p),
+                ("leaf_qbox", ctypes.c_void_p), ("leaf_origin", ctypes.c_void_p), ("node_qbox", ctypes.c_void_p),
+                ("node_child", ctypes.c_void_p), ("root", ctypes.c_void_p)]
 
 
 class hacc_sr_params(ctypes.Structure):
@@ -80,6 +87,12 @@ SIGNATURES = {
     "hacc_lists_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh)]),
     "hacc_build_lists": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists), _P, ctypes.c_size_t,
                                         _P, _P]),
+    "hacc_rcb_build_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh), ctypes.c_int32]),
+    "hacc_rcb_build": (ctypes.c_int, [_PS(hacc_mesh), _P, _P, _P, _P, _PS(hacc_tree), _PS(hacc_binned), _P,
+                                      ctypes.c_size_t, _P, _P]),
+    "hacc_rcb_lists_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh), ctypes.c_int64, ctypes.c_int64]),
+    "hacc_rcb_lists": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_tree), _PS(hacc_lists), ctypes.c_int64, _P, _P,
+                                      ctypes.c_size_t, _P, _P]),
     "hacc_force_workspace_size": (ctypes.c_size_t, [_PS(hacc_mesh)]),
     "hacc_sr_force": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists), _PS(hacc_sr_params),
                                      _P, _P, _P, _PS(hacc_launch), _P, ctypes.c_size_t, _P, _P]),

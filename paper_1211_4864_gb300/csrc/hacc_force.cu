@@ -54,6 +54,7 @@ struct KArgs {
     const int4 *tasks;
     const int32_t *order;  // task_order: heaviest first
     const int32_t *n_tasks;
+    const float4 *origin;  // per cell (leaf) origin, or NULL: chaining-mesh cell c sits at c w
     const float4 *pos;   // sorted (ox, oy, oz, m)
     const float4 *lam;   // sorted (lx, ly, lz, 0), adjoint only
     const int32_t *perm;
@@ -465,6 +466,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
     const double Ld = (double)vol.L;
     const int64_t lc = (int64_t)c - vol.cell_base;
     const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+    const float4 org_i = a.origin ? a.origin[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 
     float4 oi[IPL];
     bool active[IPL];
@@ -495,13 +497,21 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             const int sh = a.nbr_shift[g0 + lane];
             jb = a.cell_start[cp];
             cnt = a.cell_start[cp + 1] - jb;
-            const int64_t lp = (int64_t)cp - vol.cell_base;
-            const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
             const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-            // exact in float64: origins are the float32 products used by the binning
-            Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-            Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-            Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+            if (a.origin) {
+                // tree leaves: float32 origins, difference and image exact in float64
+                const float4 org_j = a.origin[cp];
+                Dx = (float)((double)org_j.x - (double)org_i.x + sx * Ld);
+                Dy = (float)((double)org_j.y - (double)org_i.y + sy * Ld);
+                Dz = (float)((double)org_j.z - (double)org_i.z + sz * Ld);
+            } else {
+                const int64_t lp = (int64_t)cp - vol.cell_base;
+                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
+                // exact in float64: origins are the float32 products used by the binning
+                Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
+                Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
+                Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+            }
         }
         int pk = 0, poff = 0;  // producer cursor (entry, record within it)
         int ck = 0, coff = 0;  // consumer cursor
@@ -653,18 +663,27 @@ k_count_pairs(const KArgs a, unsigned long long *__restrict__ total)
         const double Ld = (double)vol.L;
         const int64_t lc = (int64_t)task.x - vol.cell_base;
         const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+        const float4 org_i = a.origin ? a.origin[task.x] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = task.y + lane; i - lane < task.z; i += 32) {
             const bool active = i < task.z;
             const float4 oi = active ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int64_t e = a.nbr_off[task.x]; e < a.nbr_off[task.x + 1]; ++e) {
                 const int cp = a.nbr_cell[e];
                 const int sh = a.nbr_shift[e];
-                const int64_t lp = (int64_t)cp - vol.cell_base;
-                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
                 const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-                const float Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                const float Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                const float Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                float Dx, Dy, Dz;
+                if (a.origin) {
+                    const float4 org_j = a.origin[cp];
+                    Dx = (float)((double)org_j.x - (double)org_i.x + sx * Ld);
+                    Dy = (float)((double)org_j.y - (double)org_i.y + sy * Ld);
+                    Dz = (float)((double)org_j.z - (double)org_i.z + sz * Ld);
+                } else {
+                    const int64_t lp = (int64_t)cp - vol.cell_base;
+                    const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
+                    Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
+                    Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
+                    Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                }
                 const float oxp = oi.x - Dx, oyp = oi.y - Dy, ozp = oi.z - Dz;
                 for (int j = a.cell_start[cp]; j < a.cell_start[cp + 1]; ++j) {
                     const float4 p = a.pos[j];
@@ -795,6 +814,33 @@ int check_common(const hacc_mesh *mesh, const hacc_binned *b, const hacc_lists *
 }  // namespace
 }  // namespace hacc
 
+namespace hacc {
+namespace {
+
+// Arguments every pair kernel shares: the volumes, cells (or leaves), lists and tasks.
+KArgs base_args(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists, const hacc_sr_params *p,
+                uint32_t *status)
+{
+    KArgs a{};
+    a.vols = mesh->vols;
+    a.cell_start = binned->cell_start;
+    a.nbr_off = lists->nbr_off;
+    a.nbr_cell = lists->nbr_cell;
+    a.nbr_shift = lists->nbr_shift;
+    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
+    a.order = lists->task_order;
+    a.n_tasks = lists->n_tasks;
+    a.origin = reinterpret_cast<const float4 *>(binned->cell_origin);
+    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
+    a.perm = binned->perm;
+    a.status = status;
+    pair_consts(p, a.k);
+    return a;
+}
+
+}  // namespace
+}  // namespace hacc
+
 using namespace hacc;
 
 extern "C" size_t hacc_force_workspace_size(const hacc_mesh *mesh)
@@ -812,25 +858,11 @@ extern "C" int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, c
     if (mesh->N == 0) return HACC_OK;
     cudaStream_t st = as_stream(stream);
     ForceWs F = force_layout(mesh, ws);
-    KArgs a{};
-    a.vols = mesh->vols;
-    a.cell_start = binned->cell_start;
-    a.nbr_off = lists->nbr_off;
-    a.nbr_cell = lists->nbr_cell;
-    a.nbr_shift = lists->nbr_shift;
-    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
-    a.order = lists->task_order;
-    a.n_tasks = lists->n_tasks;
-    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
-    a.lam = nullptr;
-    a.perm = binned->perm;
+    KArgs a = base_args(mesh, binned, lists, p, status);
     a.out_x = ax;
     a.out_y = ay;
     a.out_z = az;
-    a.out_m = nullptr;
     a.counter = F.counter;
-    a.status = status;
-    pair_consts(p, a.k);
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(FORCE);
     return launch_mode<FORCE>(a, L, st);
@@ -852,25 +884,13 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     if (g > num_sms() * 16) g = num_sms() * 16;
     k_gather_lam<<<g, 256, 0, st>>>(mesh->N, binned->perm, gax, gay, gaz, F.lam);
     HACC_LAUNCH_CHECK();
-    KArgs a{};
-    a.vols = mesh->vols;
-    a.cell_start = binned->cell_start;
-    a.nbr_off = lists->nbr_off;
-    a.nbr_cell = lists->nbr_cell;
-    a.nbr_shift = lists->nbr_shift;
-    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
-    a.order = lists->task_order;
-    a.n_tasks = lists->n_tasks;
-    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
+    KArgs a = base_args(mesh, binned, lists, p, status);
     a.lam = F.lam;
-    a.perm = binned->perm;
     a.out_x = gx;
     a.out_y = gy;
     a.out_z = gz;
     a.out_m = gm;
     a.counter = F.counter;
-    a.status = status;
-    pair_consts(p, a.k);
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(ADJOINT);
     if (gm) return launch_mode<ADJOINT_GM>(a, L, st);
@@ -887,21 +907,9 @@ extern "C" int hacc_sr_potential(const hacc_mesh *mesh, const hacc_binned *binne
     if (mesh->N == 0) return HACC_OK;
     cudaStream_t st = as_stream(stream);
     ForceWs F = force_layout(mesh, ws);
-    KArgs a{};
-    a.vols = mesh->vols;
-    a.cell_start = binned->cell_start;
-    a.nbr_off = lists->nbr_off;
-    a.nbr_cell = lists->nbr_cell;
-    a.nbr_shift = lists->nbr_shift;
-    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
-    a.order = lists->task_order;
-    a.n_tasks = lists->n_tasks;
-    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
-    a.perm = binned->perm;
+    KArgs a = base_args(mesh, binned, lists, p, status);
     a.out_x = phi;
     a.counter = F.counter;
-    a.status = status;
-    pair_consts(p, a.k);
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(FORCE);
     return launch_mode<POTENTIAL>(a, L, st);
@@ -917,16 +925,7 @@ extern "C" int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned
     cudaStream_t st = as_stream(stream);
     HACC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
     if (mesh->N == 0) return HACC_OK;
-    KArgs a{};
-    a.vols = mesh->vols;
-    a.cell_start = binned->cell_start;
-    a.nbr_off = lists->nbr_off;
-    a.nbr_cell = lists->nbr_cell;
-    a.nbr_shift = lists->nbr_shift;
-    a.tasks = reinterpret_cast<const int4 *>(lists->tasks);
-    a.n_tasks = lists->n_tasks;
-    a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
-    pair_consts(p, a.k);
+    KArgs a = base_args(mesh, binned, lists, p, nullptr);
     k_count_pairs<<<num_sms() * 8, 256, 0, st>>>(a, reinterpret_cast<unsigned long long *>(out));
     HACC_LAUNCH_CHECK();
     return HACC_OK;

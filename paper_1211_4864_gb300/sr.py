@@ -19,7 +19,7 @@ import torch
 
 from . import _lib
 from ._lib import (HaccError, check, hacc_binned, hacc_launch, hacc_lists, hacc_mesh, hacc_sr_params,
-                   hacc_volume)
+                   hacc_tree, hacc_volume)
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -112,6 +112,19 @@ def hacc_build_lists(mesh, binned, lists, ws, status):
                                        ws.numel(), _ptr(status), _stream()), "hacc_build_lists")
 
 
+def hacc_rcb_build(mesh, x, y, z, m, tree, binned, ws, status):
+    """RCB fat-leaf tree (synchronises the current stream once per tree level)."""
+    check(_lib.load().hacc_rcb_build(ctypes.byref(mesh), _ptr(x), _ptr(y), _ptr(z), _ptr(m), ctypes.byref(tree),
+                                     ctypes.byref(binned), _ptr(ws), ws.numel(), _ptr(status), _stream()),
+          "hacc_rcb_build")
+
+
+def hacc_rcb_lists(mesh, tree, lists, entry_cap: int, n_entries, ws, status):
+    check(_lib.load().hacc_rcb_lists(ctypes.byref(mesh), ctypes.byref(tree), ctypes.byref(lists), int(entry_cap),
+                                     _ptr(n_entries), _ptr(ws), ws.numel(), _ptr(status), _stream()),
+          "hacc_rcb_lists")
+
+
 def hacc_sr_force(mesh, binned, lists, params: SRParams, ax, ay, az, ws, status, launch: Launch | None = None):
     p = params.c_struct()
     lc = launch.c_struct() if launch is not None else None
@@ -168,7 +181,14 @@ class ShortRange:
     """
 
     def __init__(self, L, vol_off, rcut: float, cell_min: float | None = None, split_T: int = 32,
-                 device: str | torch.device = "cuda"):
+                 device: str | torch.device = "cuda", builder: str = "mesh", leaf_max: int = 64,
+                 max_depth: int = 48):
+        """builder: "mesh" (chaining mesh, hacc_bin + hacc_build_lists) or "rcb"
+        (the paper's RCB fat-leaf tree, hacc_rcb_build + hacc_rcb_lists, leaves
+        of at most leaf_max particles; its build synchronises the stream)."""
+        if builder not in ("mesh", "rcb"):
+            raise HaccError(f"unknown list builder {builder!r}")
+        self.builder = builder
         self.device = torch.device(device)
         self.rcut = float(rcut)
         self.cell_min = float(cell_min if cell_min is not None else rcut)
@@ -185,38 +205,92 @@ class ShortRange:
         i32, i64 = torch.int32, torch.int64
         N = self.N
         self.cell_of = torch.empty(N, dtype=i32, device=dev)
-        self.cell_start = torch.empty(self.n_cells + 1, dtype=i32, device=dev)
         self.perm = torch.empty(N, dtype=i32, device=dev)
         self.sorted4 = torch.empty((N, 4), dtype=torch.float32, device=dev)
-        self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.cell_start), _ptr(self.perm), _ptr(self.sorted4))
         self.split_T = int(split_T)
-        self.task_cap = int(lib.hacc_task_capacity(ctypes.byref(self.mesh), self.split_T))
-        self.nbr_off = torch.empty(self.n_cells + 1, dtype=i64, device=dev)
-        self.nbr_cell = torch.empty(self.n_entries, dtype=i32, device=dev)
-        self.nbr_shift = torch.empty(self.n_entries, dtype=torch.int8, device=dev)
-        self.tasks = torch.empty((max(self.task_cap, 1), 4), dtype=i32, device=dev)
         self.n_tasks = torch.zeros(1, dtype=i32, device=dev)
         self.n_pairs = torch.zeros(1, dtype=i64, device=dev)
+        if builder == "mesh":
+            self.cell_start = torch.empty(self.n_cells + 1, dtype=i32, device=dev)
+            self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.cell_start), _ptr(self.perm),
+                                      _ptr(self.sorted4), None)
+            self.task_cap = int(lib.hacc_task_capacity(ctypes.byref(self.mesh), self.split_T))
+            self.nbr_off = torch.empty(self.n_cells + 1, dtype=i64, device=dev)
+            self.entry_cap = self.n_entries
+            build_ws = max(lib.hacc_bin_workspace_size(ctypes.byref(self.mesh)),
+                           lib.hacc_lists_workspace_size(ctypes.byref(self.mesh)))
+        else:
+            # a leaf holds at least one particle: N leaves (and fewer internal nodes) always fit
+            self.leaf_cap = lc = max(N, 1)
+            self.n_leaves = torch.zeros(1, dtype=i32, device=dev)
+            self.n_nodes = torch.zeros(1, dtype=i32, device=dev)
+            self.cell_start = self.leaf_start = torch.empty(lc + 1, dtype=i32, device=dev)
+            self.leaf_qbox = torch.empty((lc, 6), dtype=i32, device=dev)
+            self.leaf_origin = torch.empty((lc, 4), dtype=torch.float32, device=dev)
+            self.node_qbox = torch.empty((lc, 6), dtype=i32, device=dev)
+            self.node_child = torch.empty((lc, 2), dtype=i32, device=dev)
+            self.root = torch.empty(self.V, dtype=i32, device=dev)
+            self.tree = hacc_tree(int(leaf_max), int(max_depth), lc, _ptr(self.n_leaves), _ptr(self.n_nodes),
+                                  _ptr(self.leaf_start), _ptr(self.leaf_qbox), _ptr(self.leaf_origin),
+                                  _ptr(self.node_qbox), _ptr(self.node_child), _ptr(self.root))
+            self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.leaf_start), _ptr(self.perm),
+                                      _ptr(self.sorted4), _ptr(self.leaf_origin))
+            # each leaf gives ceil(size / T) tasks
+            self.task_cap = lc + N // self.split_T + 1
+            self.nbr_off = torch.empty(lc + 1, dtype=i64, device=dev)
+            self.n_entries_dev = torch.zeros(1, dtype=i64, device=dev)
+            self.entry_cap = 0
+            self._lstatus = torch.zeros(1, dtype=i32, device=dev)
+            build_ws = max(lib.hacc_rcb_build_workspace_size(ctypes.byref(self.mesh), int(leaf_max)),
+                           lib.hacc_rcb_lists_workspace_size(ctypes.byref(self.mesh), lc, self.task_cap))
+        self.tasks = torch.empty((max(self.task_cap, 1), 4), dtype=i32, device=dev)
         self.task_order = torch.empty(max(self.task_cap, 1), dtype=i32, device=dev)
-        self.lists = hacc_lists(_ptr(self.nbr_off), _ptr(self.nbr_cell), _ptr(self.nbr_shift), _ptr(self.tasks),
-                                _ptr(self.n_tasks), _ptr(self.n_pairs), _ptr(self.task_order), self.task_cap,
-                                self.split_T, 0)
-        ws_bytes = max(lib.hacc_bin_workspace_size(ctypes.byref(self.mesh)),
-                       lib.hacc_lists_workspace_size(ctypes.byref(self.mesh)),
-                       lib.hacc_force_workspace_size(ctypes.byref(self.mesh)),
+        self._alloc_entries(self.entry_cap)
+        ws_bytes = max(build_ws, lib.hacc_force_workspace_size(ctypes.byref(self.mesh)),
                        lib.hacc_moments_workspace_size(N))
         self.ws = torch.empty(int(ws_bytes), dtype=torch.uint8, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
 
+    def _alloc_entries(self, cap: int):
+        self.entry_cap = int(cap)
+        self.nbr_cell = torch.empty(max(self.entry_cap, 1), dtype=torch.int32, device=self.device)
+        self.nbr_shift = torch.empty(max(self.entry_cap, 1), dtype=torch.int8, device=self.device)
+        self.lists = hacc_lists(_ptr(self.nbr_off), _ptr(self.nbr_cell), _ptr(self.nbr_shift), _ptr(self.tasks),
+                                _ptr(self.n_tasks), _ptr(self.n_pairs), _ptr(self.task_order), self.task_cap,
+                                self.split_T, 0)
+
     # -- calls ------------------------------------------------------------
     def bin(self, x, y, z, m, disp=None):
+        if self.builder != "mesh":
+            raise HaccError("bin() belongs to the chaining mesh; the tree is built by prepare()")
         if disp is None:
             hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status)
         else:
             hacc_bin(self.mesh, x, y, z, m, self.binned, self.ws, self.status, disp[0], disp[1], disp[2])
 
     def build_lists(self):
+        if self.builder != "mesh":
+            raise HaccError("build_lists() belongs to the chaining mesh; the tree is built by prepare()")
         hacc_build_lists(self.mesh, self.binned, self.lists, self.ws, self.status)
+
+    def build_tree(self, x, y, z, m):
+        """RCB tree and its leaf lists (builder "rcb").  Synchronises: the build
+        reads the number of groups left per level, and the lists grow to fit."""
+        hacc_rcb_build(self.mesh, x, y, z, m, self.tree, self.binned, self.ws, self.status)
+        self.check_status()  # a tree that ran out of capacity must not be walked
+        while True:
+            self._lstatus.zero_()
+            hacc_rcb_lists(self.mesh, self.tree, self.lists, self.entry_cap, self.n_entries_dev, self.ws,
+                           self._lstatus)
+            need = int(self.n_entries_dev.item())
+            if need <= self.entry_cap:
+                break
+            self._alloc_entries(need + need // 4 + 1024)
+        s = int(self._lstatus.item())
+        if s:
+            raise HaccError(f"device status {s:#x} from the tree lists")
+        self.n_entries = need
+        self.n_cells = int(self.n_leaves.item())
 
     def force(self, params: SRParams, out=None, launch: Launch | None = None):
         if out is None:
@@ -280,6 +354,11 @@ class ShortRange:
     def prepare(self, pos, m, disp=None):
         """Binning and lists for positions pos [3, N] (plus displacements disp
         [3, N], if given: the position is then pos + disp) and masses m [N]."""
+        if self.builder == "rcb":
+            if disp is not None:
+                raise HaccError("the tree builder takes absolute positions only")
+            self.build_tree(pos[0], pos[1], pos[2], m)
+            return
         self.bin(pos[0], pos[1], pos[2], m, disp)
         self.build_lists()
 

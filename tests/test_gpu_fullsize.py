@@ -135,3 +135,26 @@ def test_batched256_sampled_volumes():
                               prm.c.astype(np.float64), tg)
         rms, mx = err_norms(A[b:e][tg], ref)
         assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
+
+
+def test_clustered256_rcb_tree_bit_exact_and_forces(clustered):
+    """The RCB fat-leaf tree of the full clustered workload: tree bit-exact, the
+    lists of sampled leaves bit-exact, forces equal to the chaining mesh's to
+    float32 rounding on every particle and to the oracle on samples."""
+    from test_gpu_rcb import check_tree_bit_exact
+    torch, hs, w, prm = clustered["torch"], clustered["hs"], clustered["w"], clustered["prm"]
+    tr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=64, builder="rcb", leaf_max=64)
+    tr.prepare(clustered["pos"], clustered["m"])
+    a = tr.force(prm, launch=clustered["launch"])
+    torch.cuda.synchronize()
+    tr.check_status()
+    check_tree_bit_exact(tr, w, 64, list_targets=12)
+    A, M = a.cpu().numpy().T.astype(np.float64), clustered["a"].cpu().numpy().T.astype(np.float64)
+    rms, mx = err_norms(A, M)
+    # two float32 sums of the same pairs in different orders: each within the oracle tolerances
+    assert rms < 1e-6 and mx < MAX_TOL, (rms, mx)
+    rng = np.random.default_rng(11)
+    tg = rng.choice(w.N, 128, replace=False)
+    ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    rms, mx = err_norms(A[tg], ref)
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)

@@ -34,8 +34,17 @@ if ROOT not in sys.path:
 FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
 # DRAM bytes of one force launch on clustered256, from ncu (profiles/force_clustered256_dram.md),
 # valid only for the kernel source it was measured on
-FORCE_TRAFFIC = {"workload": "clustered256", "bytes": 2135359744 + 954669056,
-                 "source_sha256": "bdbf9e97b5bcdf6404fa932e3933ef6e6ce0d6fac93b51186583535264282613"}
+# flops per evaluated unordered pair of the symmetric kernel: d 3, s 5, s + eps 1, t^3 2, Horner 10,
+# subtract 1, x m_j and x m_i 2, both accumulations 12
+FLOPS_PER_SYM_PAIR = 36
+# ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
+# they were taken from (null in the bench line once a source changes)
+FORCE_TRAFFIC = {
+    "gather": {"workload": "clustered256", "bytes": None, "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
+               "sha256": None},
+    "symmetric": {"workload": "clustered256", "bytes": None, "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
+                  "sha256": None},
+}
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
 WORKLOADS = {
@@ -66,6 +75,9 @@ def parse():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation measurement")
     ap.add_argument("--no-sks", action="store_true", help="skip the sub-cycle (SKS) measurement")
     ap.add_argument("--no-tree", action="store_true", help="skip the RCB tree vs chaining mesh comparison")
+    ap.add_argument("--kernel", choices=["symmetric", "gather"], default="symmetric",
+                    help="pair kernel of the timed step: Newton-III symmetric (each pair once, applied to "
+                         "both particles) or gather (each particle sums its own list)")
     ap.add_argument("--leaf-max", type=int, default=64, help="RCB leaf size bound of the tree comparison")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the step: force-kernel rate vs neighbour-list length and occupancy")
@@ -176,9 +188,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def tuned(config: str):
-    """(launch shape, split threshold) from the autotuner's cache, if tuned."""
+    """(force launch shape, split threshold, adjoint launch, symmetric launch) from the autotuner's
+    cache, if tuned."""
     from paper_1211_4864_gb300 import autotune
-    return autotune.cached(config), autotune.cached_split(config, default=64), autotune.cached(config, "adjoint")
+    return (autotune.cached(config), autotune.cached_split(config, default=64), autotune.cached(config, "adjoint"),
+            autotune.cached(config, "symmetric"))
 
 
 def run_ours(args):
@@ -193,7 +207,7 @@ def run_ours(args):
     hs.load()
     w = make_config(args.config)
     prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
-    launch, split_T, launch_adj = tuned(args.config)
+    launch, split_T, launch_adj, launch_sym = tuned(args.config)
     sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=split_T, device=dev)
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device=dev)
     m = torch.tensor(w.m, device=dev)
@@ -207,11 +221,14 @@ def run_ours(args):
     mom = torch.empty(9, dtype=torch.float64, device=dev)
     use_graph = args.graph == "on" or (args.graph == "auto" and args.config == "batched256")
 
+    force_fn = sr.force_symmetric if args.kernel == "symmetric" else sr.force
+    launch_step = launch_sym if args.kernel == "symmetric" else launch
+
     def step(k=None):
         sr.prepare(pos, m)
         if k is not None:
             f0[k].record(stream)
-        sr.force(prm, a, launch=launch)
+        force_fn(prm, a, launch=launch_step)
         if k is not None:
             f1[k].record(stream)
         sr.kick(v, a, w.dt)
@@ -280,7 +297,8 @@ def run_ours(args):
                       "list_efficiency": within / pairs if pairs else None, "replicas": ranks.world,
                       "l2": f"inputs larger than L2 (sorted float4 {16 * w.N / 1e6:.0f} MB + SoA positions "
                             f"{12 * w.N / 1e6:.0f} MB vs 126 MB L2); no flush between steps",
-                      "launch": launch.__dict__ if launch else "default", "split_T": split_T,
+                      "pair_kernel": args.kernel,
+                      "launch": launch_step.__dict__ if launch_step else "default", "split_T": split_T,
                       "cuda_graph": graph is not None,
                       "parallelism": "replicas" if ranks.world > 1 else "single GPU"},
            "gpu_launches": int(launches), "clocks": clk,
@@ -296,15 +314,27 @@ def run_ours(args):
         pass
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * 128 * 2 * f_max * 1e6 / 1e12
-    achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
-    out["roofline"] = {"bound": "alu", "kernel": "k_pairs<FORCE> (hacc_sr_force)", "achieved": achieved,
+    if args.kernel == "symmetric":
+        # executed work: each unordered candidate pair once, FLOPS_PER_SYM_PAIR flops
+        achieved = FLOPS_PER_SYM_PAIR * (pairs / 2) / (t_force * 1e-3) / 1e12
+        kname, fpp = "k_pairs_sym (hacc_sr_force_symmetric)", {"flops_per_unordered_pair": FLOPS_PER_SYM_PAIR,
+                                                               "unordered_pairs": pairs // 2}
+    else:
+        achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
+        kname, fpp = "k_pairs<FORCE> (hacc_sr_force)", {"flops_per_pair": FLOPS_PER_PAIR}
+    out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved,
                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                       "traffic": force_traffic(args.config),
+                       "traffic": force_traffic(args.config, args.kernel),
                        "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (max SM clock)",
-                       "flops_per_pair": FLOPS_PER_PAIR, "force_ms": t_force,
-                       "force_share": t_force / (t_ms / args.steps)}
+                       **fpp, "force_ms": t_force, "force_share": t_force / (t_ms / args.steps),
+                       "interactions_29_flop_equivalent_frac": FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
+                       / peak}
     if clk.get("sm_mhz"):
         out["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    # the other pair kernel on the same lists: Newton-III symmetric vs gather
+    if ranks.rank == 0:
+        out["newton3"] = newton3(torch, sr, prm, launch, launch_sym, a, pairs, args.kernel, t_force, peak)
 
     # forward + adjoint on the same lists (not part of the timed step)
     lam = torch.randn((3, w.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
@@ -318,8 +348,10 @@ def run_ours(args):
     eb.record(stream)
     torch.cuda.synchronize()
     t_adj = ea.elapsed_time(eb) / 3
-    out["fwd_adjoint"] = {"force_ms": t_force, "adjoint_ms": t_adj, "ratio_fwd_plus_adj_over_fwd":
-                          (t_force + t_adj) / t_force}
+    # the pair the autograd Function uses: the gather forward and its hand-written adjoint
+    t_gather = out["newton3"]["gather_force_ms"] if "newton3" in out else t_force
+    out["fwd_adjoint"] = {"forward_kernel": "gather (hacc_sr_force)", "force_ms": t_gather, "adjoint_ms": t_adj,
+                          "ratio_fwd_plus_adj_over_fwd": (t_gather + t_adj) / t_gather}
 
     # differentiation workload: forward trajectory vs forward + backward
     if not args.no_diff and ranks.rank == 0:
@@ -327,7 +359,8 @@ def run_ours(args):
 
     # the paper's RCB fat-leaf tree as the list builder, against the chaining mesh
     if not args.no_tree and ranks.rank == 0 and w.V == 1:
-        out["tree_vs_mesh"] = tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs, within,
+        t_gather = out["newton3"]["gather_force_ms"] if "newton3" in out else t_force
+        out["tree_vs_mesh"] = tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_gather, pairs, within,
                                            args.leaf_max)
 
     # short-range sub-cycles of the split-operator step: throughput and drift
@@ -336,11 +369,11 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     if not args.no_e2e:
-        out["e2e"] = e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs)
+        out["e2e"] = e2e(args, torch, hs, sr, w, prm, force_fn, launch_step, dev, ranks, pairs)
 
     # sampled float64 oracle check of this run's forces (untimed)
     if not args.no_check and ranks.rank == 0:
-        out["error_vs_oracle"] = check_sample(sr, pos, m, prm, w, launch)
+        out["error_vs_oracle"] = check_sample(sr, pos, m, prm, w, force_fn, launch_step)
 
     if ranks.rank == 0 and ranks.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, prm, args.cpu_sample)
@@ -394,22 +427,58 @@ def differentiation(torch, hs, reps: int = 3):
             "forward_ms": t_f, "forward_backward_ms": t_fb, "ratio_fwd_bwd_over_fwd": t_fb / t_f}
 
 
-def force_traffic(config: str):
-    """Recorded ncu DRAM bytes per force launch, or None if the kernel source changed since."""
+def kernel_sources_sha(kernel: str) -> str:
     import hashlib
-    src = os.path.join(ROOT, "paper_1211_4864_gb300", "csrc", "hacc_force.cu")
+    h = hashlib.sha256()
+    for name in FORCE_TRAFFIC[kernel]["sources"]:
+        h.update(open(os.path.join(ROOT, "paper_1211_4864_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
+def force_traffic(config: str, kernel: str):
+    """Recorded ncu DRAM bytes per force launch, or None if the kernel's sources changed since."""
+    rec = FORCE_TRAFFIC[kernel]
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = kernel_sources_sha(kernel)
     except OSError:
         return None
-    if config != FORCE_TRAFFIC["workload"] or sha != FORCE_TRAFFIC["source_sha256"]:
+    if config != rec["workload"] or sha != rec["sha256"]:
         return None
-    return FORCE_TRAFFIC["bytes"]
+    return rec["bytes"]
+
+
+def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, reps=3):
+    """Gather kernel (every particle sums its own list: each pair evaluated
+    twice) against the Newton-III symmetric kernel (each pair once, applied to
+    both), same lists, same inputs; the one the step did not use is timed
+    here, and the forces of the two are compared."""
+    other = sr.force if kernel == "symmetric" else sr.force_symmetric
+    l_other = launch if kernel == "symmetric" else launch_sym
+    b = torch.empty_like(a)
+    other(prm, b, launch=l_other)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        other(prm, b, launch=l_other)
+    e1.record()
+    torch.cuda.synchronize()
+    sr.check_status()
+    t_other = e0.elapsed_time(e1) / reps
+    t_g, t_s = (t_other, t_force) if kernel == "symmetric" else (t_force, t_other)
+    rel = float((a.double() - b.double()).norm() / b.double().norm())
+    return {"gather_force_ms": t_g, "symmetric_force_ms": t_s, "speedup": t_g / t_s,
+            "interactions_per_s": {"gather": pairs / (t_g * 1e-3), "symmetric": pairs / (t_s * 1e-3)},
+            "fp32_frac_executed": {"gather": FLOPS_PER_PAIR * pairs / (t_g * 1e-3) / 1e12 / peak,
+                                   "symmetric": FLOPS_PER_SYM_PAIR * pairs / 2 / (t_s * 1e-3) / 1e12 / peak},
+            "force_rel_diff": rel,
+            "launch": {"gather": launch.__dict__ if launch else "default",
+                       "symmetric": launch_sym.__dict__ if launch_sym else "default"}}
 
 
 def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs, within, leaf_max, reps=3):
-    """Same positions, same pair kernel, lists from the RCB fat-leaf tree
-    (Sec. III) instead of the chaining mesh: build, walk and force times,
+    """Same positions, same (gather) pair kernel, lists from the RCB fat-leaf
+    tree (Sec. III) instead of the chaining mesh: build, walk and force times,
     candidate and within-cutoff pairs, and the force difference between the
     two (float32 rounding only: both visit every pair inside the cutoff)."""
     tr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=split_T, builder="rcb", leaf_max=leaf_max)
@@ -513,7 +582,7 @@ def sks_measure(torch, hs, n_c: int = 10, h: float = 0.01):
             "momentum_drift": float(np.linalg.norm(p1 - p0))}
 
 
-def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
+def e2e(args, torch, hs, sr, w, prm, force_fn, launch, dev, ranks, pairs):
     """Same step with inputs in pinned host memory, copies inside the timed region."""
     host_in = torch.tensor(np.stack([w.x, w.y, w.z, w.m, w.vx, w.vy, w.vz]).astype(np.float32)).pin_memory()
     host_out = torch.empty((3, w.N), dtype=torch.float32).pin_memory()
@@ -528,7 +597,7 @@ def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
         m = dbuf[3]
         v = dbuf[4:7]
         sr.prepare(pos, m)
-        sr.force(prm, a, launch=launch)
+        force_fn(prm, a, launch=launch)
         sr.kick(v, a, w.dt)
         mom = sr.moments(m, v, a)
         host_out.copy_(v, non_blocking=True)
@@ -552,13 +621,13 @@ def e2e(args, torch, hs, sr, w, prm, launch, dev, ranks, pairs):
             "d2h_bytes_per_step": int(host_out.numel() * 4 + host_mom.numel() * 8)}
 
 
-def check_sample(sr, pos, m, prm, w, launch, S=256):
+def check_sample(sr, pos, m, prm, w, force_fn, launch, S=256):
     import torch
 
     import oracle
     if w.V != 1:
         return None
-    a = sr.force(prm, launch=launch)
+    a = force_fn(prm, launch=launch)
     torch.cuda.synchronize()
     rng = np.random.default_rng(11)
     tg = rng.choice(w.N, size=min(S, w.N), replace=False)

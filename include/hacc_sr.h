@@ -294,6 +294,22 @@ int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_l
                   const hacc_launch *launch, void *ws, size_t ws_bytes, uint32_t *status,
                   void *stream);
 
+/* Same forces as hacc_sr_force from half the pair evaluations: each pair
+ * inside the cutoff is evaluated once and applied to both particles
+ * (Newton's third law; the paper's kernel instead evaluates every particle's
+ * own list, Sec. III).  Each task walks its cell itself and the entries after
+ * the cell in its list (the stencil is symmetric); a warp holds 32 j records
+ * one per lane and rotates them, with their force partial sums, through the
+ * lanes by shuffles; the partial sums are added to float64 per-particle
+ * totals with atomics, converted to float32 at the end.  Chaining-mesh lists
+ * only (binned->cell_origin must be NULL).  Results agree with hacc_sr_force
+ * to float32 rounding but are not bitwise reproducible (the float64 sums
+ * are formed in a run-dependent order).  Workspace: hacc_force_workspace_size. */
+int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
+                            const hacc_sr_params *p, float *ax, float *ay, float *az,
+                            const hacc_launch *launch, void *ws, size_t ws_bytes, uint32_t *status,
+                            void *stream);
+
 /* Vector-Jacobian product of hacc_sr_force (not in the paper).  Given
  * lam = dL/da (gax, gay, gaz, [N] input order) returns, in input order,
  *   gx_i = dL/dx_i = sum_j [m_i J(d_ij) lam_j - m_j J(d_ij) lam_i],

@@ -101,8 +101,9 @@ def tune(run, config: str, mode: str = "force", quick: bool = False, reps: int =
 
 
 def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str = CACHE) -> dict:
-    """Tune split threshold and launch shape of the force and adjoint kernels
-    on one of the standard workloads (synth.make_config names)."""
+    """Tune split threshold and launch shape of the force kernel, then the
+    launch shapes of the adjoint and the symmetric force kernel on the chosen
+    lists, for one of the standard workloads (synth.make_config names)."""
     import numpy as np
     import torch
 
@@ -135,6 +136,9 @@ def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str =
     La, _ = tune(lambda L: sr.adjoint(prm, lam, want_gm=False, launch=L), config, mode="adjoint", quick=True,
                  write=False)
     ent["adjoint"] = {"launch": La.__dict__}
+    Ls, tab_s = tune(lambda L: sr.force_symmetric(prm, out, launch=L), config, mode="symmetric", quick=quick,
+                     write=False)
+    ent["symmetric"] = {"launch": Ls.__dict__, "ms": min(t[1] for t in tab_s if t[1] is not None)}
     with open(path, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
     return {"best": ent, "table": report}

@@ -133,6 +133,16 @@ def hacc_sr_force(mesh, binned, lists, params: SRParams, ax, ay, az, ws, status,
                                     ws.numel(), _ptr(status), _stream()), "hacc_sr_force")
 
 
+def hacc_sr_force_symmetric(mesh, binned, lists, params: SRParams, ax, ay, az, ws, status,
+                            launch: Launch | None = None):
+    p = params.c_struct()
+    lc = launch.c_struct() if launch is not None else None
+    check(_lib.load().hacc_sr_force_symmetric(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
+                                              ctypes.byref(p), _ptr(ax), _ptr(ay), _ptr(az),
+                                              ctypes.byref(lc) if lc else None, _ptr(ws), ws.numel(), _ptr(status),
+                                              _stream()), "hacc_sr_force_symmetric")
+
+
 def hacc_sr_force_adjoint(mesh, binned, lists, params: SRParams, gax, gay, gaz, gx, gy, gz, gm, ws, status,
                           launch: Launch | None = None):
     p = params.c_struct()
@@ -297,6 +307,17 @@ class ShortRange:
             out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
         hacc_sr_force(self.mesh, self.binned, self.lists, params, out[0], out[1], out[2], self.ws, self.status,
                       launch)
+        return out
+
+    def force_symmetric(self, params: SRParams, out=None, launch: Launch | None = None):
+        """Same forces from half the pair evaluations (Newton's third law;
+        chaining mesh only; not bitwise reproducible)."""
+        if self.builder != "mesh":
+            raise HaccError("the symmetric kernel needs the chaining mesh's lists")
+        if out is None:
+            out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
+        hacc_sr_force_symmetric(self.mesh, self.binned, self.lists, params, out[0], out[1], out[2], self.ws,
+                                self.status, launch)
         return out
 
     def adjoint(self, params: SRParams, lam, out=None, want_gm: bool = True, launch: Launch | None = None):

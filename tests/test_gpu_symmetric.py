@@ -1,0 +1,126 @@
+"""GPU parity of the Newton-III symmetric pair kernel (hacc_sr_force_symmetric):
+the same forces as the gather kernel and the float64 oracle from half the
+pair evaluations, on uniform, clustered, fine-mesh, small-box and batched
+inputs, every launch shape, and tiny task sizes."""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import MAX_TOL, RMS_TOL, err_norms, need_cuda
+from synth import default_coeffs, uniform_box
+from synth.workloads import Workload, batched_volumes, clustered_box
+
+pytestmark = pytest.mark.gpu
+
+EPS, RC = 0.01, 3.0
+SHAPES = [(8, 3, 32, 2), (8, 3, 32, 4), (8, 3, 64, 2), (8, 3, 64, 3), (8, 3, 64, 4), (8, 3, 128, 2),
+          (8, 3, 128, 3), (4, 3, 128, 4), (8, 3, 256, 2)]
+
+
+@pytest.fixture(scope="module")
+def hs():
+    need_cuda()
+    import paper_1211_4864_gb300 as hs
+    hs.load()
+    return hs
+
+
+def params(hs):
+    return hs.SRParams(EPS, RC, default_coeffs(RC, EPS))
+
+
+def run_both(hs, w: Workload, cell_min=None, split_T=64, launch=None):
+    import torch
+    prm = params(hs)
+    sr = hs.ShortRange(w.L, w.vol_off, RC, cell_min=cell_min, split_T=split_T)
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    m = torch.tensor(w.m, device="cuda")
+    sr.prepare(pos, m)
+    a_s = sr.force_symmetric(prm, launch=launch)
+    a_g = sr.force(prm)
+    mom = sr.moments(m, None, a_s).cpu().numpy()
+    torch.cuda.synchronize()
+    sr.check_status()
+    return sr, a_s.cpu().numpy().T.astype(np.float64), a_g.cpu().numpy().T.astype(np.float64), mom
+
+
+def oracle_force(w: Workload, v=0, targets=None):
+    b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+    c = default_coeffs(RC, EPS).astype(np.float64)
+    return oracle.sr_force(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), EPS, RC, c, targets)
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered", "fine_mesh", "small_box", "tiny_tasks"])
+def test_symmetric_against_oracle_and_gather(hs, case):
+    cell_min, split_T = None, 64
+    if case == "uniform":
+        w = uniform_box(4096, 16.0, seed=1)
+    elif case == "clustered":
+        w = clustered_box(20, 4, seed=21)
+    elif case == "fine_mesh":  # reach 2: 125 list entries per cell, the forward half spans several groups
+        w, cell_min = uniform_box(3000, 14.0, seed=18), 1.5
+    elif case == "small_box":  # n = 3 cells per side: every neighbour is a periodic image
+        w = uniform_box(1500, 9.0, seed=19)
+    else:  # chunks of 7 particles: many tasks per cell, every diagonal block ragged
+        w, split_T = clustered_box(16, 3, seed=22), 7
+    rng = np.random.default_rng(5)
+    w.m[:] = rng.uniform(0.5, 1.5, w.N).astype(np.float32)
+    sr, a_s, a_g, mom = run_both(hs, w, cell_min=cell_min, split_T=split_T)
+    ref = oracle_force(w)
+    rms, mx = err_norms(a_s, ref)
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+    rms, mx = err_norms(a_s, a_g)
+    assert rms < 1e-6 and mx < MAX_TOL, (rms, mx)
+    # Newton's third law holds by construction: the net force vanishes to float64 rounding of the sums
+    assert np.all(np.abs(mom[3:6]) < 1e-6 * mom[7]), mom
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_symmetric_every_launch_shape(hs, shape):
+    w = clustered_box(16, 3, seed=23)
+    launch = hs.Launch(*shape)
+    _, a_s, a_g, _ = run_both(hs, w, launch=launch)
+    rms, mx = err_norms(a_s, a_g)
+    assert rms < 1e-6 and mx < MAX_TOL, (shape, rms, mx)
+
+
+def test_symmetric_batched_volumes(hs):
+    w = batched_volumes(12, n_lo=800, n_hi=6000, seed=7)
+    _, a_s, _, _ = run_both(hs, w)
+    for v in range(w.V):
+        b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+        rms, mx = err_norms(a_s[b:e], oracle_force(w, v))
+        assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
+
+
+def test_symmetric_empty_volume_and_empty_input(hs):
+    import torch
+    wa, wb = uniform_box(700, 10.0, seed=31), uniform_box(900, 11.0, seed=32)
+    cat = lambda f: np.concatenate([getattr(wa, f), getattr(wb, f)])
+    w = Workload("gap", cat("x"), cat("y"), cat("z"), cat("m"), cat("vx"), cat("vy"), cat("vz"),
+                 np.array([10.0, 9.5, 11.0], np.float32), np.array([0, 700, 700, 1600], np.int64))
+    _, a_s, _, _ = run_both(hs, w)
+    for v, (b, e) in ((0, (0, 700)), (2, (700, 1600))):
+        rms, mx = err_norms(a_s[b:e], oracle_force(w, v))
+        assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
+    prm = params(hs)
+    sr = hs.ShortRange(np.array([12.0], np.float32), np.array([0, 0], np.int64), RC)
+    empty = torch.zeros((3, 0), device="cuda")
+    sr.prepare(empty, torch.zeros(0, device="cuda"))
+    a = sr.force_symmetric(prm)
+    torch.cuda.synchronize()
+    sr.check_status()
+    assert a.shape == (3, 0)
+
+
+def test_symmetric_rejects_tree_lists(hs):
+    import torch
+    w = uniform_box(1000, 12.0, seed=3)
+    sr = hs.ShortRange(w.L, w.vol_off, RC, builder="rcb", leaf_max=32)
+    sr.prepare(torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda"), torch.tensor(w.m, device="cuda"))
+    with pytest.raises(hs.HaccError):
+        sr.force_symmetric(params(hs))
+    sr.builder = "mesh"  # bypass the binding's check: the library itself refuses leaf origins
+    with pytest.raises(hs.HaccError):
+        sr.force_symmetric(params(hs))

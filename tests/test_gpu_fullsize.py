@@ -21,7 +21,8 @@ pytestmark = pytest.mark.gpu
 
 def _tuned(config):
     from paper_1211_4864_gb300 import autotune
-    return autotune.cached(config), autotune.cached_split(config, 64), autotune.cached(config, "adjoint")
+    return (autotune.cached(config), autotune.cached_split(config, 64), autotune.cached(config, "adjoint"),
+            autotune.cached(config, "symmetric"))
 
 
 def _setup(config):
@@ -29,7 +30,7 @@ def _setup(config):
     import paper_1211_4864_gb300 as hs
     hs.load()
     w = make_config(config)
-    launch, T, launch_adj = _tuned(config)
+    launch, T, launch_adj, launch_sym = _tuned(config)
     prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
     sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
@@ -38,7 +39,8 @@ def _setup(config):
     a = sr.force(prm, launch=launch)
     torch.cuda.synchronize()
     sr.check_status()
-    return dict(torch=torch, hs=hs, w=w, prm=prm, sr=sr, pos=pos, m=m, a=a, launch=launch, launch_adj=launch_adj)
+    return dict(torch=torch, hs=hs, w=w, prm=prm, sr=sr, pos=pos, m=m, a=a, launch=launch, launch_adj=launch_adj,
+                launch_sym=launch_sym)
 
 
 @pytest.fixture(scope="module")
@@ -79,6 +81,26 @@ def test_clustered256_forces_sampled(clustered):
     got = clustered["a"].cpu().numpy().T[tg].astype(np.float64)
     rms, mx = err_norms(got, ref)
     assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+
+
+def test_clustered256_symmetric_kernel_sampled_and_against_gather(clustered):
+    """The Newton-III symmetric kernel in the benchmark's launch shape: every
+    particle against the gather kernel, samples against the oracle, zero net
+    force."""
+    torch, w, prm, sr = clustered["torch"], clustered["w"], clustered["prm"], clustered["sr"]
+    s = sr.force_symmetric(prm, launch=clustered["launch_sym"])
+    mom = sr.moments(clustered["m"], None, s).cpu().numpy()
+    torch.cuda.synchronize()
+    sr.check_status()
+    S = s.cpu().numpy().T.astype(np.float64)
+    rms, mx = err_norms(S, clustered["a"].cpu().numpy().T.astype(np.float64))
+    assert rms < 1e-6 and mx < MAX_TOL, (rms, mx)
+    ob = oracle.bin_volume(w.x, w.y, w.z, w.m, float(w.L[0]), w.cell_min)
+    tg = sample_targets(ob["cell_start"], ob["perm"], w.N, 256, crowded_cells=16, per_cell=4, seed=8)
+    ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
+    rms, mx = err_norms(S[tg], ref)
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+    assert np.all(np.abs(mom[3:6]) < 1e-6 * mom[7]), mom
 
 
 def test_clustered256_newton_third_law(clustered):
@@ -126,6 +148,12 @@ def test_batched256_sampled_volumes():
     w, prm, sr = ctx["w"], ctx["prm"], ctx["sr"]
     ctx["table_base"] = [ctx["sr"].table[v].cell_base for v in range(w.V)]
     A = ctx["a"].cpu().numpy().T.astype(np.float64)
+    S = sr.force_symmetric(prm, launch=ctx["launch_sym"])
+    ctx["torch"].cuda.synchronize()
+    sr.check_status()
+    S = S.cpu().numpy().T.astype(np.float64)
+    rms, mx = err_norms(S, A)  # the symmetric kernel over all 256 volumes against the gather kernel
+    assert rms < 1e-6 and mx < MAX_TOL, (rms, mx)
     rng = np.random.default_rng(6)
     for v in sorted(set([0, 127, 128, 255]) | set(rng.choice(w.V, 4, replace=False).tolist())):
         _bin_bit_exact(ctx, v)
@@ -134,6 +162,8 @@ def test_batched256_sampled_volumes():
         ref = oracle.sr_force(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), prm.eps, prm.rcut,
                               prm.c.astype(np.float64), tg)
         rms, mx = err_norms(A[b:e][tg], ref)
+        assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
+        rms, mx = err_norms(S[b:e][tg], ref)
         assert rms < RMS_TOL and mx < MAX_TOL, (v, rms, mx)
 
 

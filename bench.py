@@ -190,11 +190,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def tuned(config: str):
-    """(force launch shape, split threshold, adjoint launch, symmetric launch) from the autotuner's
-    cache, if tuned."""
+    """(force launch shape, split threshold, adjoint launch, symmetric launch, symmetric adjoint
+    launch) from the autotuner's cache, if tuned."""
     from paper_1211_4864_gb300 import autotune
     return (autotune.cached(config), autotune.cached_split(config, default=64), autotune.cached(config, "adjoint"),
-            autotune.cached(config, "symmetric"))
+            autotune.cached(config, "symmetric"), autotune.cached(config, "adjoint_symmetric"))
 
 
 def run_ours(args):
@@ -209,7 +209,7 @@ def run_ours(args):
     hs.load()
     w = make_config(args.config)
     prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
-    launch, split_T, launch_adj, launch_sym = tuned(args.config)
+    launch, split_T, launch_adj, launch_sym, launch_adj_sym = tuned(args.config)
     sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=split_T, device=dev)
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device=dev)
     m = torch.tensor(w.m, device=dev)
@@ -350,10 +350,23 @@ def run_ours(args):
     eb.record(stream)
     torch.cuda.synchronize()
     t_adj = ea.elapsed_time(eb) / 3
-    # the pair the autograd Function uses: the gather forward and its hand-written adjoint
+    # the two forward/adjoint pairs the autograd Function can use, on the same lists
     t_gather = out["newton3"]["gather_force_ms"] if "newton3" in out else t_force
+    t_symf = out["newton3"]["symmetric_force_ms"] if "newton3" in out else t_force
+    sr.adjoint_symmetric(prm, lam, want_gm=False, launch=launch_adj_sym)
+    torch.cuda.synchronize()
+    ea.record(stream)
+    for _ in range(3):
+        sr.adjoint_symmetric(prm, lam, want_gm=False, launch=launch_adj_sym)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    sr.check_status()
+    t_adj_sym = ea.elapsed_time(eb) / 3
     out["fwd_adjoint"] = {"forward_kernel": "gather (hacc_sr_force)", "force_ms": t_gather, "adjoint_ms": t_adj,
-                          "ratio_fwd_plus_adj_over_fwd": (t_gather + t_adj) / t_gather}
+                          "ratio_fwd_plus_adj_over_fwd": (t_gather + t_adj) / t_gather,
+                          "symmetric": {"force_ms": t_symf, "adjoint_ms": t_adj_sym,
+                                        "ratio_fwd_plus_adj_over_fwd": (t_symf + t_adj_sym) / t_symf,
+                                        "adjoint_speedup_vs_gather": t_adj / t_adj_sym}}
 
     # differentiation workload: forward trajectory vs forward + backward
     if not args.no_diff and ranks.rank == 0:
@@ -398,14 +411,16 @@ def differentiation(torch, hs, reps: int = 3):
     wt = torch.tensor(w.extra["loss_w"].T.copy(), device="cuda")
     steps = int(w.extra["steps"])
 
+    sym = [False]
+
     def fwd():
         with torch.no_grad():
-            d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps)
+            d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps, symmetric=sym[0])
             return (wt * d * d).sum()
 
     def fwd_bwd():
         x0.grad = v0.grad = m.grad = None
-        d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps)
+        d, _ = hs.trajectory_autograd(x0, v0, m, sr, prm, w.dt, steps, symmetric=sym[0])
         loss = (wt * d * d).sum()
         loss.backward()
         return loss
@@ -423,10 +438,16 @@ def differentiation(torch, hs, reps: int = 3):
 
     t_f = timed(fwd)
     t_fb = timed(fwd_bwd)
+    sym[0] = True
+    t_fs = timed(fwd)
+    t_fbs = timed(fwd_bwd)
     sr.check_status()
     return {"workload": "diff64: 64^3 = 262,144 particles, L = 64, 60% uniform + 40% in 100 NFW halos "
                         "(seed 4), 4 kick-drift steps of dt = 0.01, loss sum w (x_4 - x_0)^2",
-            "forward_ms": t_f, "forward_backward_ms": t_fb, "ratio_fwd_bwd_over_fwd": t_fb / t_f}
+            "pair_kernels": "gather (hacc_sr_force + hacc_sr_force_adjoint)",
+            "forward_ms": t_f, "forward_backward_ms": t_fb, "ratio_fwd_bwd_over_fwd": t_fb / t_f,
+            "symmetric": {"pair_kernels": "hacc_sr_force_symmetric + hacc_sr_force_adjoint_symmetric",
+                          "forward_ms": t_fs, "forward_backward_ms": t_fbs, "ratio_fwd_bwd_over_fwd": t_fbs / t_fs}}
 
 
 def kernel_sources_sha(kernel: str) -> str:

@@ -310,6 +310,18 @@ int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned *binned, co
                             const hacc_launch *launch, void *ws, size_t ws_bytes, uint32_t *status,
                             void *stream);
 
+/* hacc_sr_force_adjoint with each pair evaluated once: the pair's terms of
+ * dL/dx are antisymmetric (J(d) is even in d), so the j side receives minus
+ * the i side's, and both sides keep the factored sums U, V, X, G of the
+ * gather adjoint (float64 totals by atomics, as hacc_sr_force_symmetric).
+ * Same arguments and outputs as hacc_sr_force_adjoint; chaining-mesh lists
+ * only; not bitwise reproducible.  Not in the paper. */
+int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc_binned *binned,
+                                    const hacc_lists *lists, const hacc_sr_params *p, const float *gax,
+                                    const float *gay, const float *gaz, float *gx, float *gy, float *gz,
+                                    float *gm, const hacc_launch *launch, void *ws, size_t ws_bytes,
+                                    uint32_t *status, void *stream);
+
 /* Vector-Jacobian product of hacc_sr_force (not in the paper).  Given
  * lam = dL/da (gax, gay, gaz, [N] input order) returns, in input order,
  *   gx_i = dL/dx_i = sum_j [m_i J(d_ij) lam_j - m_j J(d_ij) lam_i],

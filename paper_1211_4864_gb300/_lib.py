@@ -99,6 +99,9 @@ SIGNATURES = {
     "hacc_sr_force_symmetric": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists),
                                                _PS(hacc_sr_params), _P, _P, _P, _PS(hacc_launch), _P,
                                                ctypes.c_size_t, _P, _P]),
+    "hacc_sr_force_adjoint_symmetric": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists),
+                                                       _PS(hacc_sr_params), _P, _P, _P, _P, _P, _P, _P,
+                                                       _PS(hacc_launch), _P, ctypes.c_size_t, _P, _P]),
     "hacc_sr_force_adjoint": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists),
                                              _PS(hacc_sr_params), _P, _P, _P, _P, _P, _P, _P, _PS(hacc_launch),
                                              _P, ctypes.c_size_t, _P, _P]),

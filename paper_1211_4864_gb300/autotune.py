@@ -139,6 +139,11 @@ def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str =
     Ls, tab_s = tune(lambda L: sr.force_symmetric(prm, out, launch=L), config, mode="symmetric", quick=quick,
                      write=False)
     ent["symmetric"] = {"launch": Ls.__dict__, "ms": min(t[1] for t in tab_s if t[1] is not None)}
+    # 128 registers per thread: at most 16 warps per SM
+    cands = [c for c in candidates(quick) if c.warps_per_cta * c.ctas_per_sm <= 16]
+    Lsa, tab_sa = tune(lambda L: sr.adjoint_symmetric(prm, lam, want_gm=False, launch=L), config,
+                       mode="adjoint_symmetric", write=False, cands=cands)
+    ent["adjoint_symmetric"] = {"launch": Lsa.__dict__, "ms": min(t[1] for t in tab_sa if t[1] is not None)}
     with open(path, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
     return {"best": ent, "table": report}

@@ -58,46 +58,6 @@ struct Acc<FORCE, IPL> : AccN<IPL, 3> {};
 template <int IPL>
 struct Acc<POTENTIAL, IPL> : AccN<IPL, 1> {};
 
-// Adjoint accumulators per i particle: U (3) = sum f lam_j, V = sum m_j f,
-// X (3) = sum fp2 (m_i d.lam_j - m_j d.lam_i) d, G = sum f d.lam_j (with dL/dm
-// only).  Float32 partial sums live in registers for one tile; the
-// compensated (hi, lo) totals live in shared memory, lane-contiguous, so that
-// two i particles per lane fit the register budget.
-template <int MODE, int IPL>
-struct AccAdj {
-    static constexpr int NACC = MODE == ADJOINT_GM ? 8 : 7;
-    float p[IPL][ADJ_NACC];
-    float *comp;  // [IPL][NACC][hi, lo][32 lanes]
-    int lane;
-    __device__ __forceinline__ float &hi(int u, int k) const { return comp[((u * NACC + k) * 2 + 0) * 32 + lane]; }
-    __device__ __forceinline__ float &lo(int u, int k) const { return comp[((u * NACC + k) * 2 + 1) * 32 + lane]; }
-    __device__ __forceinline__ AccAdj(float *c, int ln) : comp(c), lane(ln)
-    {
-#pragma unroll
-        for (int u = 0; u < IPL; ++u)
-#pragma unroll
-            for (int k = 0; k < ADJ_NACC; ++k) p[u][k] = 0.f;
-#pragma unroll
-        for (int u = 0; u < IPL; ++u)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) hi(u, k) = lo(u, k) = 0.f;
-    }
-    __device__ __forceinline__ void fold()
-    {
-#pragma unroll
-        for (int u = 0; u < IPL; ++u)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) {
-                float h = hi(u, k), l = lo(u, k);
-                two_sum_acc(h, l, p[u][k]);
-                hi(u, k) = h;
-                lo(u, k) = l;
-                p[u][k] = 0.f;
-            }
-    }
-    __device__ __forceinline__ float total(int u, int k) const { return hi(u, k) + lo(u, k); }
-};
-
 // One pair of the forward law, accumulated into acc[3].  The cutoff test is
 // a compare whose predicate guards the three accumulating fma (no branch, no
 // select): the paper folds the same test into the loop with fsel (Sec. III).
@@ -439,18 +399,6 @@ __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
             ring.drain();
             return;
         }
-    }
-}
-
-// Sorted cotangent records (lx, ly, lz, 0) for the adjoint.
-__global__ void __launch_bounds__(256)
-k_gather_lam(int64_t N, const int32_t *__restrict__ perm, const float *__restrict__ gx,
-             const float *__restrict__ gy, const float *__restrict__ gz, float4 *__restrict__ lam)
-{
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int i = perm[k];
-        lam[k] = make_float4(gx[i], gy[i], gz[i], 0.f);
     }
 }
 

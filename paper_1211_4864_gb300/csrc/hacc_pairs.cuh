@@ -126,6 +126,59 @@ constexpr int ADJ_NACC = 8;
 constexpr int ADJ_IPL_MAX = 2;
 constexpr int ADJ_COMP_BYTES = ADJ_IPL_MAX * ADJ_NACC * 2 * 32 * 4;
 
+// Adjoint accumulators per i particle: U (3) = sum f lam_j, V = sum m_j f,
+// X (3) = sum fp2 (m_i d.lam_j - m_j d.lam_i) d, G = sum f d.lam_j (with dL/dm
+// only).  Float32 partial sums live in registers for one tile; the
+// compensated (hi, lo) totals live in shared memory, lane-contiguous, so that
+// two i particles per lane fit the register budget.
+template <int MODE, int IPL>
+struct AccAdj {
+    static constexpr int NACC = MODE == ADJOINT_GM ? 8 : 7;
+    float p[IPL][ADJ_NACC];
+    float *comp;  // [IPL][NACC][hi, lo][32 lanes]
+    int lane;
+    __device__ __forceinline__ float &hi(int u, int k) const { return comp[((u * NACC + k) * 2 + 0) * 32 + lane]; }
+    __device__ __forceinline__ float &lo(int u, int k) const { return comp[((u * NACC + k) * 2 + 1) * 32 + lane]; }
+    __device__ __forceinline__ AccAdj(float *c, int ln) : comp(c), lane(ln)
+    {
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < ADJ_NACC; ++k) p[u][k] = 0.f;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) hi(u, k) = lo(u, k) = 0.f;
+    }
+    __device__ __forceinline__ void fold()
+    {
+#pragma unroll
+        for (int u = 0; u < IPL; ++u)
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) {
+                float h = hi(u, k), l = lo(u, k);
+                two_sum_acc(h, l, p[u][k]);
+                hi(u, k) = h;
+                lo(u, k) = l;
+                p[u][k] = 0.f;
+            }
+    }
+    __device__ __forceinline__ float total(int u, int k) const { return hi(u, k) + lo(u, k); }
+};
+
+
+// Sorted cotangent records (lx, ly, lz, 0) for the adjoint.
+__global__ void __launch_bounds__(256)
+k_gather_lam(int64_t N, const int32_t *__restrict__ perm, const float *__restrict__ gx,
+             const float *__restrict__ gy, const float *__restrict__ gz, float4 *__restrict__ lam)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int i = perm[k];
+        lam[k] = make_float4(gx[i], gy[i], gz[i], 0.f);
+    }
+}
+
 // Shared memory of one warp: STAGES tiles (two arrays in the adjoint),
 // STAGES mbarriers and, in the adjoint, the compensated totals; padded so
 // that every warp's tiles start 128-B aligned.
@@ -238,9 +291,11 @@ void pair_consts(const hacc_sr_params *p, PairConsts &K)
     }
 }
 
-// Workspace of the pair calls: the task counter, then one region that the
-// adjoint uses for its sorted cotangents (16 B per particle) and the
-// symmetric kernel for its float64 force sums (3 x 8 B per particle).
+// Workspace of the pair calls: the task counter, the adjoints' sorted
+// cotangents (16 B per particle), and the symmetric kernels' float64 sums
+// (3 per particle for the force, 8 for the adjoint).
+constexpr int SYM_ACC_MAX = 8;
+
 struct ForceWs {
     int32_t *counter;
     float4 *lam;
@@ -252,10 +307,11 @@ ForceWs force_layout(const hacc_mesh *mesh, void *ws)
 {
     ForceWs F{};
     char *p = reinterpret_cast<char *>(ws);
+    const size_t lam_bytes = round_up((size_t)mesh->N * 16, 256);
     F.counter = reinterpret_cast<int32_t *>(p);
     F.lam = reinterpret_cast<float4 *>(p ? p + 256 : nullptr);
-    F.acc = reinterpret_cast<double *>(p ? p + 256 : nullptr);
-    F.total = 256 + round_up((size_t)mesh->N * 24, 256);
+    F.acc = reinterpret_cast<double *>(p ? p + 256 + lam_bytes : nullptr);
+    F.total = 256 + lam_bytes + round_up((size_t)mesh->N * 8 * SYM_ACC_MAX, 256);
     return F;
 }
 

@@ -153,6 +153,17 @@ def hacc_sr_force_adjoint(mesh, binned, lists, params: SRParams, gax, gay, gaz, 
                                             ws.numel(), _ptr(status), _stream()), "hacc_sr_force_adjoint")
 
 
+def hacc_sr_force_adjoint_symmetric(mesh, binned, lists, params: SRParams, gax, gay, gaz, gx, gy, gz, gm, ws,
+                                    status, launch: Launch | None = None):
+    p = params.c_struct()
+    lc = launch.c_struct() if launch is not None else None
+    check(_lib.load().hacc_sr_force_adjoint_symmetric(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
+                                                      ctypes.byref(p), _ptr(gax), _ptr(gay), _ptr(gaz), _ptr(gx),
+                                                      _ptr(gy), _ptr(gz), _ptr(gm),
+                                                      ctypes.byref(lc) if lc else None, _ptr(ws), ws.numel(),
+                                                      _ptr(status), _stream()), "hacc_sr_force_adjoint_symmetric")
+
+
 def hacc_count_pairs(mesh, binned, lists, params: SRParams, out):
     p = params.c_struct()
     check(_lib.load().hacc_count_pairs(ctypes.byref(mesh), ctypes.byref(binned), ctypes.byref(lists),
@@ -330,6 +341,20 @@ class ShortRange:
                               out[2], gm, self.ws, self.status, launch)
         return out, gm
 
+    def adjoint_symmetric(self, params: SRParams, lam, out=None, want_gm: bool = True,
+                          launch: Launch | None = None):
+        """adjoint() with each pair evaluated once (chaining mesh only; not
+        bitwise reproducible)."""
+        if self.builder != "mesh":
+            raise HaccError("the symmetric adjoint needs the chaining mesh's lists")
+        if out is None:
+            out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
+        gm = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_gm else None
+        lam = lam.contiguous()
+        hacc_sr_force_adjoint_symmetric(self.mesh, self.binned, self.lists, params, lam[0], lam[1], lam[2], out[0],
+                                        out[1], out[2], gm, self.ws, self.status, launch)
+        return out, gm
+
     def kick(self, v, a, dt_kick, pos=None, dt_drift=0.0, wrap=True):
         """v += dt_kick a; then pos += dt_drift v (wrapped into the boxes if wrap)."""
         if pos is None:
@@ -406,12 +431,13 @@ class ShortRange:
 
 class _SRForce(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, pos, disp, m, solver: ShortRange, params: SRParams):
+    def forward(ctx, pos, disp, m, solver: ShortRange, params: SRParams, symmetric: bool):
         solver.prepare(pos, m, disp)
-        a = solver.force(params)
+        a = solver.force_symmetric(params) if symmetric else solver.force(params)
         ctx.save_for_backward(pos, disp, m)
         ctx.solver = solver
         ctx.params = params
+        ctx.symmetric = symmetric
         return a
 
     @staticmethod
@@ -420,9 +446,10 @@ class _SRForce(torch.autograd.Function):
         solver = ctx.solver
         # the pair terms are recomputed: re-bin the saved positions, then the adjoint
         solver.prepare(pos, m, disp)
-        gpos, gm = solver.adjoint(ctx.params, ga.contiguous(), want_gm=ctx.needs_input_grad[2])
+        adj = solver.adjoint_symmetric if ctx.symmetric else solver.adjoint
+        gpos, gm = adj(ctx.params, ga.contiguous(), want_gm=ctx.needs_input_grad[2])
         # the position is pos + disp: both receive the same cotangent
-        return gpos, gpos if ctx.needs_input_grad[1] else None, gm, None, None
+        return gpos, gpos if ctx.needs_input_grad[1] else None, gm, None, None, None
 
 
 class _KickDrift(torch.autograd.Function):
@@ -455,11 +482,13 @@ class _KickDrift(torch.autograd.Function):
         return gv, gp2, ga, None, None
 
 
-def sr_force_autograd(pos, m, solver: ShortRange, params: SRParams, disp=None):
+def sr_force_autograd(pos, m, solver: ShortRange, params: SRParams, disp=None, symmetric: bool = False):
     """Accelerations [3, N] at positions pos [3, N] (+ disp [3, N] if given);
-    differentiable in pos, disp and m."""
+    differentiable in pos, disp and m.  symmetric: the Newton-III kernels
+    (each pair evaluated once) for the forward and the adjoint; otherwise the
+    gather kernels (bitwise reproducible)."""
     return _SRForce.apply(pos.contiguous(), None if disp is None else disp.contiguous(), m.contiguous(), solver,
-                          params)
+                          params, bool(symmetric))
 
 
 def kick_drift_autograd(v, pos, a, dt_k: float, dt_d: float):
@@ -467,16 +496,17 @@ def kick_drift_autograd(v, pos, a, dt_k: float, dt_d: float):
     return _KickDrift.apply(v.contiguous(), pos.contiguous(), a.contiguous(), dt_k, dt_d)
 
 
-def trajectory_autograd(x0, v0, m, solver: ShortRange, params: SRParams, dt: float, steps: int):
+def trajectory_autograd(x0, v0, m, solver: ShortRange, params: SRParams, dt: float, steps: int,
+                        symmetric: bool = False):
     """`steps` short-range kick-drift steps (the kick and stream maps of the
     paper's split-operator step, Eq. 6) from positions x0 [3, N] and velocities
     v0 [3, N].  Positions stay x0 + disp with a float32 displacement that the
     drift updates, so they keep float32 precision of the displacement rather
     than of the box.  Returns (disp, v) after the last step; differentiable in
-    x0, v0 and m."""
+    x0, v0 and m (symmetric: see sr_force_autograd)."""
     disp = torch.zeros_like(x0)
     v = v0
     for _ in range(steps):
-        a = sr_force_autograd(x0, m, solver, params, disp)
+        a = sr_force_autograd(x0, m, solver, params, disp, symmetric)
         v, disp = kick_drift_autograd(v, disp, a, dt, dt)
     return disp, v

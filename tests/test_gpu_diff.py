@@ -1,6 +1,7 @@
 """Differentiation: gradients of a four-step short-range trajectory through the
 hand-written adjoint (torch.autograd.Function over the C ABI) against the
-float64 oracle's reference gradient and float64 finite differences.
+float64 oracle's reference gradient and float64 finite differences, with the
+gather kernels and with the Newton-III symmetric kernels.
 
 Loss: sum_i w_i . (x_S,i - x_0,i)^2 over S kick-drift steps of dt (the kick
 and stream maps of the paper's split-operator step, Eq. 6), w seeded N(0, 1).
@@ -22,8 +23,8 @@ GRAD_RMS_TOL = 1e-5    # GPU float32 gradient vs float64 reference gradient
 FD_REL_TOL = 1e-3      # GPU float32 gradient vs float64 finite differences
 
 
-@pytest.fixture(scope="module")
-def case():
+@pytest.fixture(scope="module", params=[False, True], ids=["gather", "symmetric"])
+def case(request):
     torch = need_cuda()
     import paper_1211_4864_gb300 as hs
     hs.load()
@@ -37,7 +38,7 @@ def case():
     x0 = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda", requires_grad=True)
     vt = torch.tensor(v0.T.copy(), device="cuda", requires_grad=True)
     mt = torch.tensor(w.m, device="cuda", requires_grad=True)
-    disp, v = hs.trajectory_autograd(x0, vt, mt, sr, prm, DT, STEPS)
+    disp, v = hs.trajectory_autograd(x0, vt, mt, sr, prm, DT, STEPS, symmetric=request.param)
     wt_t = torch.tensor(wt.T.astype(np.float32), device="cuda")
     loss = (wt_t * disp * disp).sum()
     loss.backward()

@@ -40,12 +40,12 @@ FLOPS_PER_SYM_PAIR = 36
 # ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
 # they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2133740800 + 953634304,
+    "gather": {"workload": "clustered256", "bytes": 2133427712 + 953597952,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "719a0c0654e362005a5dbc8e47916d4b1616d56dc750ff9eb07cd37631d0bfaf"},
-    "symmetric": {"workload": "clustered256", "bytes": 2695868928 + 1422654464,
+               "sha256": "718e24bc8f68bb0827cfae2c79daa0e94fcba58b0665c240da026706163e1b70"},
+    "symmetric": {"workload": "clustered256", "bytes": 2695881728 + 1420933888,
                   "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
-                  "sha256": "f80a94d70ef4ff6666360563ab7218f4d7187915ec5c5a10c1fecde431acd2cc"},
+                  "sha256": "d9ace8e4d55d7b2deba115a8720bdffe75b14da975097fc08409644e39b26cce"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

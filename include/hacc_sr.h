@@ -359,7 +359,8 @@ int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned, const hac
  *   v <- v + dt_kick a;  then, if x != NULL, x <- x + dt_drift v (new v),
  * the drift computed in float64 and rounded once to float32.  If `mesh` is
  * non-NULL the drifted positions are wrapped into [0, L) of their volume.
- * Arrays [N] in input order; x, y, z may be NULL (kick only). */
+ * Arrays [N] in input order; x, y, z may be NULL (kick only); ax, ay, az may
+ * be NULL (the stream map alone: v is read, never written); not both. */
 int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy, float *vz, const float *ax,
               const float *ay, const float *az, float dt_kick, float *x, float *y, float *z,
               float dt_drift, void *stream);

@@ -14,12 +14,15 @@ k_kick(int64_t N, float *__restrict__ vx, float *__restrict__ vy, float *__restr
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float nvx = fmaf(dtk, ax[i], vx[i]);
-        float nvy = fmaf(dtk, ay[i], vy[i]);
-        float nvz = fmaf(dtk, az[i], vz[i]);
-        vx[i] = nvx;
-        vy[i] = nvy;
-        vz[i] = nvz;
+        float nvx = vx[i], nvy = vy[i], nvz = vz[i];
+        if (ax) {  // no accelerations: the stream map alone (velocities unchanged)
+            nvx = fmaf(dtk, ax[i], nvx);
+            nvy = fmaf(dtk, ay[i], nvy);
+            nvz = fmaf(dtk, az[i], nvz);
+            vx[i] = nvx;
+            vy[i] = nvy;
+            vz[i] = nvz;
+        }
         if (x) {
             double px = (double)x[i] + dtd * (double)nvx;
             double py = (double)y[i] + dtd * (double)nvy;
@@ -115,8 +118,10 @@ extern "C" int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy,
 {
     if (N < 0) return HACC_ERR_INVALID;
     if (N == 0) return HACC_OK;
-    if (!vx || !vy || !vz || !ax || !ay || !az) return HACC_ERR_INVALID;
+    if (!vx || !vy || !vz) return HACC_ERR_INVALID;
+    if ((ax || ay || az) && !(ax && ay && az)) return HACC_ERR_INVALID;
     if ((x || y || z) && !(x && y && z)) return HACC_ERR_INVALID;
+    if (!ax && !x) return HACC_ERR_INVALID;  // neither a kick nor a drift
     if (mesh && (!mesh->vols || mesh->N != N)) return HACC_ERR_INVALID;
     int64_t g = (N + 255) / 256;
     if (g > (int64_t)num_sms() * 16) g = (int64_t)num_sms() * 16;

@@ -363,6 +363,11 @@ class ShortRange:
             hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], a[0], a[1], a[2], dt_kick, pos[0],
                       pos[1], pos[2], dt_drift)
 
+    def stream(self, v, pos, dt, wrap=True):
+        """The stream map alone: pos += dt v (float64, wrapped if wrap); v unchanged."""
+        hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], None, None, None, 0.0, pos[0], pos[1],
+                  pos[2], dt)
+
     def moments(self, m, v=None, a=None, phi=None):
         """FP64 [sum m v (3), sum m a (3), kinetic energy, sum m |a|, potential energy]."""
         out = torch.empty(9, dtype=torch.float64, device=self.device)
@@ -389,9 +394,8 @@ class ShortRange:
         is a library kernel, so the sequence can be captured in a CUDA graph."""
         if a is None:
             a = torch.empty_like(v)
-        zero = a  # dt_kick = 0: the stream map leaves v unchanged
         for _ in range(n_c):
-            self.kick(v, zero, 0.0, pos, 0.5 * h)
+            self.stream(v, pos, 0.5 * h)
             self.prepare(pos, m)
             self.force(params, a, launch=launch)
             self.kick(v, a, h, pos, 0.5 * h)

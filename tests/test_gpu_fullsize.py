@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 def _tuned(config):
     from paper_1211_4864_gb300 import autotune
     return (autotune.cached(config), autotune.cached_split(config, 64), autotune.cached(config, "adjoint"),
-            autotune.cached(config, "symmetric"))
+            autotune.cached(config, "symmetric"), autotune.cached(config, "adjoint_symmetric"))
 
 
 def _setup(config):
@@ -30,7 +30,7 @@ def _setup(config):
     import paper_1211_4864_gb300 as hs
     hs.load()
     w = make_config(config)
-    launch, T, launch_adj, launch_sym = _tuned(config)
+    launch, T, launch_adj, launch_sym, launch_adj_sym = _tuned(config)
     prm = hs.SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
     sr = hs.ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
@@ -40,7 +40,7 @@ def _setup(config):
     torch.cuda.synchronize()
     sr.check_status()
     return dict(torch=torch, hs=hs, w=w, prm=prm, sr=sr, pos=pos, m=m, a=a, launch=launch, launch_adj=launch_adj,
-                launch_sym=launch_sym)
+                launch_sym=launch_sym, launch_adj_sym=launch_adj_sym)
 
 
 @pytest.fixture(scope="module")
@@ -125,6 +125,30 @@ def test_clustered256_adjoint_sampled_and_translation_invariant(clustered):
     rms, _ = err_norms(G[tg], rg)
     assert rms < RMS_TOL, rms
     assert np.linalg.norm(gm.cpu().numpy()[tg] - rgm) / np.linalg.norm(rgm) < RMS_TOL
+
+
+def test_clustered256_symmetric_adjoint_sampled_and_against_gather(clustered):
+    """The symmetric adjoint in the benchmark's launch shape: every particle
+    against the gather adjoint, samples against the oracle, zero net
+    position gradient."""
+    torch, w, prm, sr = clustered["torch"], clustered["w"], clustered["prm"], clustered["sr"]
+    rng = np.random.default_rng(23)
+    lam = rng.normal(size=(w.N, 3)).astype(np.float32)
+    lt = torch.tensor(lam.T.copy(), device="cuda")
+    gs, gms = sr.adjoint_symmetric(prm, lt, launch=clustered["launch_adj_sym"])
+    gg, gmg = sr.adjoint(prm, lt, launch=clustered["launch_adj"])
+    torch.cuda.synchronize()
+    sr.check_status()
+    S, G = gs.cpu().numpy().T.astype(np.float64), gg.cpu().numpy().T.astype(np.float64)
+    assert np.linalg.norm(S.sum(0)) < 1e-6 * np.abs(S).sum()
+    rms, _ = err_norms(S, G)
+    assert rms < RMS_TOL, rms
+    tg = rng.choice(w.N, 128, replace=False)
+    rg, rgm = oracle.sr_force_adjoint(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut,
+                                      prm.c.astype(np.float64), lam, tg)
+    rms, _ = err_norms(S[tg], rg)
+    assert rms < RMS_TOL, rms
+    assert np.linalg.norm(gms.cpu().numpy()[tg] - rgm) / np.linalg.norm(rgm) < RMS_TOL
 
 
 def test_lattice128_forces_sampled_and_kick():

@@ -364,3 +364,12 @@ def test_kick_drift_against_oracle(torch, hs):
     sr.kick(vt, at, 0.0, xt2, 50.0, wrap=True)
     xs = xt2.cpu().numpy()
     assert xs.min() >= 0.0 and xs.max() < L
+    # the stream map alone (no accelerations): velocities untouched, x += dt v
+    v2 = torch.tensor(v.T.copy(), device="cuda")
+    xt3 = torch.tensor(x.T.copy(), device="cuda")
+    sr.stream(v2, xt3, 0.02, wrap=False)
+    _, x_ref3 = oracle.kick_drift(v, np.zeros_like(a), 0.0, x, 0.02)
+    assert torch.equal(v2, torch.tensor(v.T.copy(), device="cuda"))
+    assert np.allclose(xt3.cpu().numpy().T, x_ref3, rtol=0, atol=4e-6)
+    with pytest.raises(hs.HaccError):  # neither a kick nor a drift
+        hs.hacc_kick(None, N, v2[0], v2[1], v2[2], None, None, None, 0.0)

@@ -60,7 +60,8 @@ def test_sks_subcycles_against_oracle_eager_and_graph(hs):
     m = torch.tensor(w.m, device="cuda")
     pos = torch.tensor(x0.T.copy(), device="cuda")
     v = torch.tensor(v0.T.copy(), device="cuda")
-    a = torch.empty_like(v)
+    # the acceleration buffer's old contents must not matter (the stream maps never read it)
+    a = torch.full_like(v, float("nan"))
     sr.sks_subcycles(pos, v, m, prm, h, n_c, a)
     sr.prepare(pos, m)
     phi = sr.potential(prm)

@@ -375,8 +375,9 @@ def run_ours(args):
     # the paper's RCB fat-leaf tree as the list builder, against the chaining mesh
     if not args.no_tree and ranks.rank == 0 and w.V == 1:
         t_gather = out["newton3"]["gather_force_ms"] if "newton3" in out else t_force
-        out["tree_vs_mesh"] = tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_gather, pairs, within,
-                                           args.leaf_max)
+        t_symm = out["newton3"]["symmetric_force_ms"] if "newton3" in out else None
+        out["tree_vs_mesh"] = tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, launch_sym, split_T, t_gather,
+                                           t_symm, pairs, within, args.leaf_max)
 
     # short-range sub-cycles of the split-operator step: throughput and drift
     if not args.no_sks and ranks.rank == 0:
@@ -499,11 +500,13 @@ def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak,
                        "symmetric": launch_sym.__dict__ if launch_sym else "default"}}
 
 
-def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs, within, leaf_max, reps=3):
-    """Same positions, same (gather) pair kernel, lists from the RCB fat-leaf
-    tree (Sec. III) instead of the chaining mesh: build, walk and force times,
-    candidate and within-cutoff pairs, and the force difference between the
-    two (float32 rounding only: both visit every pair inside the cutoff)."""
+def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, launch_sym, split_T, t_force, t_sym, pairs, within,
+                 leaf_max, reps=3):
+    """Same positions, same pair kernels, lists from the RCB fat-leaf tree
+    (Sec. III) instead of the chaining mesh: build, walk and force times (gather
+    and symmetric kernels), candidate and within-cutoff pairs, and the force
+    difference between the two (float32 rounding only: both visit every pair
+    inside the cutoff)."""
     tr = hs.ShortRange(w.L, w.vol_off, w.rcut, split_T=split_T, builder="rcb", leaf_max=leaf_max)
     tr.prepare(pos, m)
     a_t = tr.force(prm, launch=launch)
@@ -529,6 +532,8 @@ def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs,
     t_lists = ev(lambda: hs.hacc_rcb_lists(tr.mesh, tr.tree, tr.lists, tr.entry_cap, tr.n_entries_dev, tr.ws,
                                            tr.status))
     t_tforce = ev(lambda: tr.force(prm, a_t, launch=launch))
+    a_ts = torch.empty_like(a_t)
+    t_tsym = ev(lambda: tr.force_symmetric(prm, a_ts, launch=launch_sym))
     t_prep = ev(lambda: sr.prepare(pos, m))
     a_m = sr.force(prm, launch=launch)
     torch.cuda.synchronize()
@@ -539,11 +544,13 @@ def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, split_T, t_force, pairs,
     t_within = tr.pairs_within_cutoff(prm)
     res = {"leaf_max": leaf_max, "n_leaves": int(tr.n_leaves.item()), "n_nodes": int(tr.n_nodes.item()),
            "leaf_list_entries": tr.n_entries,
-           "tree": {"build_ms": min(tb), "lists_ms": t_lists, "force_ms": t_tforce, "candidate_pairs": t_pairs,
+           "tree": {"build_ms": min(tb), "lists_ms": t_lists, "force_ms": t_tforce, "symmetric_force_ms": t_tsym,
+                    "candidate_pairs": t_pairs,
                     "pairs_within_cutoff": t_within, "list_efficiency": t_within / t_pairs,
                     "pairs_per_s": t_pairs / (t_tforce * 1e-3),
                     "within_cutoff_pairs_per_s": t_within / (t_tforce * 1e-3)},
-           "mesh": {"bin_plus_lists_ms": t_prep, "force_ms": t_force, "candidate_pairs": pairs,
+           "mesh": {"bin_plus_lists_ms": t_prep, "force_ms": t_force, "symmetric_force_ms": t_sym,
+                    "candidate_pairs": pairs,
                     "pairs_within_cutoff": within, "list_efficiency": within / pairs,
                     "pairs_per_s": pairs / (t_force * 1e-3),
                     "within_cutoff_pairs_per_s": within / (t_force * 1e-3)},

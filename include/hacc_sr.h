@@ -298,11 +298,13 @@ int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_l
  * inside the cutoff is evaluated once and applied to both particles
  * (Newton's third law; the paper's kernel instead evaluates every particle's
  * own list, Sec. III).  Each task walks its cell itself and the entries after
- * the cell in its list (the stencil is symmetric); a warp holds 32 j records
+ * the cell in its list (lists are symmetric: a chaining-mesh cell's own
+ * entry sits in the middle of its list, a tree leaf's is found by bisection
+ * of its (image, leaf) order); a warp holds 32 j records
  * one per lane and rotates them, with their force partial sums, through the
  * lanes by shuffles; the partial sums are added to float64 per-particle
- * totals with atomics, converted to float32 at the end.  Chaining-mesh lists
- * only (binned->cell_origin must be NULL).  Results agree with hacc_sr_force
+ * totals with atomics, converted to float32 at the end.  Chaining-mesh and
+ * tree lists alike.  Results agree with hacc_sr_force
  * to float32 rounding but are not bitwise reproducible (the float64 sums
  * are formed in a run-dependent order).  Workspace: hacc_force_workspace_size. */
 int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lists *lists,
@@ -314,8 +316,8 @@ int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned *binned, co
  * dL/dx are antisymmetric (J(d) is even in d), so the j side receives minus
  * the i side's, and both sides keep the factored sums U, V, X, G of the
  * gather adjoint (float64 totals by atomics, as hacc_sr_force_symmetric).
- * Same arguments and outputs as hacc_sr_force_adjoint; chaining-mesh lists
- * only; not bitwise reproducible.  Not in the paper. */
+ * Same arguments and outputs as hacc_sr_force_adjoint; chaining-mesh or
+ * tree lists; not bitwise reproducible.  Not in the paper. */
 int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc_binned *binned,
                                     const hacc_lists *lists, const hacc_sr_params *p, const float *gax,
                                     const float *gay, const float *gaz, float *gx, float *gy, float *gz,

@@ -4,10 +4,11 @@
 // antisymmetric the same way; see its section below).
 //
 // Work decomposition.  The same tasks, lists and staging ring as the gather
-// kernel, but each task walks half of its cell's stencil: the cell itself and
-// the entries after it in the canonical list (the stencil is symmetric, so
-// every other neighbour pair is met from the other cell).  Inside the cell a
-// task meets its own chunk (pairs j > i) and the particles after the chunk.
+// kernel, but each task walks half of its cell's list: the cell itself and
+// the entries after it (lists are symmetric, so every other neighbour pair is
+// met from the other cell); chaining-mesh cells and tree leaves alike.
+// Inside the cell a task meets its own chunk (pairs j > i) and the particles
+// after the chunk.
 //
 // Warp rotation.  A block of 32 j records sits one per lane, each with its
 // own force partial sums; for 32 steps every lane pairs its i particles
@@ -27,6 +28,47 @@ namespace {
 
 // Position of an empty lane: every pair with it fails the cutoff test.
 constexpr float FAR = 1.0e6f;
+
+// The list entry of cell (or leaf) c itself, image 13.  A chaining-mesh list
+// is symmetric under d -> -d with the cell in the middle; a tree leaf's list
+// is sorted by (image code, leaf id) and symmetric too (leaf j with image s
+// is listed for i iff i with image -s is listed for j), so its own entry is
+// found by bisection and everything after it is the forward half.
+__device__ __forceinline__ int64_t self_entry(const KArgs &a, int c, int64_t e0, int64_t e1, const hacc_volume &vol)
+{
+    if (!a.origin) return e0 + (vol.S - 1) / 2;
+    int64_t lo = e0, hi = e1 - 1;
+    while (lo < hi) {  // first entry with (code, leaf) >= (13, c)
+        const int64_t mid = (lo + hi) >> 1;
+        const int code = a.nbr_shift[mid], leaf = a.nbr_cell[mid];
+        if (code < 13 || (code == 13 && leaf < c)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Image offset Delta of one list entry: origin of cell (leaf) cp shifted by
+// the image, minus the origin of c; float64, rounded once.
+__device__ __forceinline__ void entry_delta(const KArgs &a, const hacc_volume &vol, int cp, int sh, int cx, int cy,
+                                            int cz, const float4 &org_i, float &Dx, float &Dy, float &Dz)
+{
+    const double Ld = (double)vol.L;
+    const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
+    if (a.origin) {
+        const float4 org_j = a.origin[cp];
+        Dx = (float)((double)org_j.x - (double)org_i.x + sx * Ld);
+        Dy = (float)((double)org_j.y - (double)org_i.y + sy * Ld);
+        Dz = (float)((double)org_j.z - (double)org_i.z + sz * Ld);
+    } else {
+        const int n = vol.n;
+        const float w = vol.w;
+        const int64_t lp = (int64_t)cp - vol.cell_base;
+        const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
+        // exact in float64: origins are the float32 products used by the binning
+        Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
+        Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
+        Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+    }
+}
 
 // One j of a rotation block: its record shifted into the i frame, its
 // sorted slot (-1: empty lane) and its force partial sums.
@@ -140,10 +182,9 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
 {
     const PairConsts &K = a.k;
     const int n = vol.n;
-    const float w = vol.w;
-    const double Ld = (double)vol.L;
     const int64_t lc = (int64_t)c - vol.cell_base;
     const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+    const float4 org_i = a.origin ? a.origin[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 
     float4 oi[IPL];
     bool active[IPL];
@@ -170,7 +211,7 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
 
     // the cell after the chunk, then the forward entries (staged)
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
-    const int64_t mid = e0 + (vol.S - 1) / 2;  // the cell itself (image 13) sits in the middle of its list
+    const int64_t mid = self_entry(a, c, e0, e1, vol);
     const int ce = a.cell_start[c + 1];
     for (int64_t g0 = mid; g0 < e1; g0 += 32) {
         const int ng = (int)min((int64_t)32, e1 - g0);
@@ -182,16 +223,9 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
                 cnt = ce - ie;
             } else {
                 const int cp = a.nbr_cell[g0 + lane];
-                const int sh = a.nbr_shift[g0 + lane];
                 jb = a.cell_start[cp];
                 cnt = a.cell_start[cp + 1] - jb;
-                const int64_t lp = (int64_t)cp - vol.cell_base;
-                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-                const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-                // exact in float64: origins are the float32 products used by the binning
-                Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                entry_delta(a, vol, cp, a.nbr_shift[g0 + lane], cx, cy, cz, org_i, Dx, Dy, Dz);
             }
         }
         int pk = 0, poff = 0;  // producer cursor
@@ -461,10 +495,9 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
     constexpr int MODE = GM ? ADJOINT_GM : ADJOINT;
     const PairConsts &K = a.k;
     const int n = vol.n;
-    const float w = vol.w;
-    const double Ld = (double)vol.L;
     const int64_t lc = (int64_t)c - vol.cell_base;
     const int cx = (int)(lc % n), cy = (int)((lc / n) % n), cz = (int)(lc / ((int64_t)n * n));
+    const float4 org_i = a.origin ? a.origin[c] : make_float4(0.f, 0.f, 0.f, 0.f);
 
     float4 oi[IPL], li[IPL];
     bool active[IPL];
@@ -492,7 +525,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
     }
 
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
-    const int64_t mid = e0 + (vol.S - 1) / 2;
+    const int64_t mid = self_entry(a, c, e0, e1, vol);
     const int ce = a.cell_start[c + 1];
     for (int64_t g0 = mid; g0 < e1; g0 += 32) {
         const int ng = (int)min((int64_t)32, e1 - g0);
@@ -504,15 +537,9 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
                 cnt = ce - ie;
             } else {
                 const int cp = a.nbr_cell[g0 + lane];
-                const int sh = a.nbr_shift[g0 + lane];
                 jb = a.cell_start[cp];
                 cnt = a.cell_start[cp + 1] - jb;
-                const int64_t lp = (int64_t)cp - vol.cell_base;
-                const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-                const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-                Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                entry_delta(a, vol, cp, a.nbr_shift[g0 + lane], cx, cy, cz, org_i, Dx, Dy, Dz);
             }
         }
         int pk = 0, poff = 0;
@@ -683,7 +710,6 @@ extern "C" int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned 
 {
     int rc = check_common(mesh, binned, lists, p, launch, ws, ws_bytes, status);
     if (rc) return rc;
-    if (binned->cell_origin) return HACC_ERR_INVALID;  // the half stencil needs the chaining mesh's lists
     if (mesh->N > 0 && (!ax || !ay || !az)) return HACC_ERR_INVALID;
     if (mesh->N == 0) return HACC_OK;
     cudaStream_t st = as_stream(stream);
@@ -718,7 +744,6 @@ extern "C" int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc
 {
     int rc = check_common(mesh, binned, lists, p, launch, ws, ws_bytes, status);
     if (rc) return rc;
-    if (binned->cell_origin) return HACC_ERR_INVALID;  // the half stencil needs the chaining mesh's lists
     if (mesh->N > 0 && (!gax || !gay || !gaz || !gx || !gy || !gz)) return HACC_ERR_INVALID;
     if (mesh->N == 0) return HACC_OK;
     cudaStream_t st = as_stream(stream);

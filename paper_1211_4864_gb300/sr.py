@@ -322,9 +322,7 @@ class ShortRange:
 
     def force_symmetric(self, params: SRParams, out=None, launch: Launch | None = None):
         """Same forces from half the pair evaluations (Newton's third law;
-        chaining mesh only; not bitwise reproducible)."""
-        if self.builder != "mesh":
-            raise HaccError("the symmetric kernel needs the chaining mesh's lists")
+        not bitwise reproducible)."""
         if out is None:
             out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
         hacc_sr_force_symmetric(self.mesh, self.binned, self.lists, params, out[0], out[1], out[2], self.ws,
@@ -343,10 +341,7 @@ class ShortRange:
 
     def adjoint_symmetric(self, params: SRParams, lam, out=None, want_gm: bool = True,
                           launch: Launch | None = None):
-        """adjoint() with each pair evaluated once (chaining mesh only; not
-        bitwise reproducible)."""
-        if self.builder != "mesh":
-            raise HaccError("the symmetric adjoint needs the chaining mesh's lists")
+        """adjoint() with each pair evaluated once (not bitwise reproducible)."""
         if out is None:
             out = torch.empty((3, self.N), dtype=torch.float32, device=self.device)
         gm = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_gm else None

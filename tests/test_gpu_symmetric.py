@@ -114,16 +114,38 @@ def test_symmetric_empty_volume_and_empty_input(hs):
     assert a.shape == (3, 0)
 
 
-def test_symmetric_rejects_tree_lists(hs):
+@pytest.mark.parametrize("case,leaf_max", [("uniform", 32), ("clustered", 64), ("clustered", 7)])
+def test_symmetric_on_tree_lists(hs, case, leaf_max):
+    """The symmetric force and adjoint on RCB leaf lists (own entry found by
+    bisection, forward half after it) against the oracle and the gather
+    kernels on the same lists."""
     import torch
-    w = uniform_box(1000, 12.0, seed=3)
-    sr = hs.ShortRange(w.L, w.vol_off, RC, builder="rcb", leaf_max=32)
-    sr.prepare(torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda"), torch.tensor(w.m, device="cuda"))
-    with pytest.raises(hs.HaccError):
-        sr.force_symmetric(params(hs))
-    sr.builder = "mesh"  # bypass the binding's check: the library itself refuses leaf origins
-    with pytest.raises(hs.HaccError):
-        sr.force_symmetric(params(hs))
+    w = uniform_box(3000, 12.0, seed=3) if case == "uniform" else clustered_box(20, 4, seed=24)
+    rng = np.random.default_rng(12)
+    w.m[:] = rng.uniform(0.5, 1.5, w.N).astype(np.float32)
+    prm = params(hs)
+    sr = hs.ShortRange(w.L, w.vol_off, RC, split_T=64, builder="rcb", leaf_max=leaf_max)
+    m = torch.tensor(w.m, device="cuda")
+    sr.prepare(torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda"), m)
+    a_s = sr.force_symmetric(prm)
+    a_g = sr.force(prm)
+    lam = rng.normal(size=(w.N, 3)).astype(np.float32)
+    lt = torch.tensor(lam.T.copy(), device="cuda")
+    g_s, gm_s = sr.adjoint_symmetric(prm, lt)
+    mom = sr.moments(m, None, a_s).cpu().numpy()
+    torch.cuda.synchronize()
+    sr.check_status()
+    S = a_s.cpu().numpy().T.astype(np.float64)
+    rms, mx = err_norms(S, oracle_force(w))
+    assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+    rms, mx = err_norms(S, a_g.cpu().numpy().T.astype(np.float64))
+    assert rms < 1e-6 and mx < MAX_TOL, (rms, mx)
+    assert np.all(np.abs(mom[3:6]) < 1e-6 * mom[7]), mom
+    c = default_coeffs(RC, EPS).astype(np.float64)
+    rg, rgm = oracle.sr_force_adjoint(w.x, w.y, w.z, w.m, float(w.L[0]), EPS, RC, c, lam)
+    rms, _ = err_norms(g_s.cpu().numpy().T, rg)
+    assert rms < RMS_TOL, rms
+    assert np.linalg.norm(gm_s.cpu().numpy() - rgm) / np.linalg.norm(rgm) < RMS_TOL
 
 
 @pytest.mark.parametrize("case,want_gm", [("uniform", True), ("clustered", True), ("clustered", False),

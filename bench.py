@@ -334,6 +334,10 @@ def run_ours(args):
     if clk.get("sm_mhz"):
         out["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
 
+    # binning: the HBM-bound kernel family of the step
+    if ranks.rank == 0:
+        out["binning"] = binning_rate(torch, sr, pos, m, w, peaks)
+
     # the other pair kernel on the same lists: Newton-III symmetric vs gather
     if ranks.rank == 0:
         out["newton3"] = newton3(torch, sr, prm, launch, launch_sym, a, pairs, args.kernel, t_force, peak)
@@ -469,6 +473,34 @@ def force_traffic(config: str, kernel: str):
     if config != rec["workload"] or sha != rec["sha256"]:
         return None
     return rec["bytes"]
+
+
+def binning_rate(torch, sr, pos, m, w, peaks, reps=5):
+    """hacc_bin and hacc_build_lists timed alone (CUDA events, mean of reps).
+    Algorithmic bytes of the binning: read x, y, z, m (16 B), write cell_of,
+    perm (8 B) and the sorted float4 record (16 B) per particle, plus 4 B of
+    cell_start per cell."""
+    def ev(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_bin = ev(lambda: sr.bin(pos[0], pos[1], pos[2], m))
+    t_lists = ev(sr.build_lists)
+    sr.check_status()
+    algo = 40 * w.N + 4 * (sr.n_cells + 1)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"bin_ms": t_bin, "lists_ms": t_lists, "algorithmic_bytes": algo,
+            "achieved_GBs": algo / (t_bin * 1e-3) / 1e9, "hbm_peak_GBs": hbm,
+            "frac": algo / (t_bin * 1e-3) / 1e9 / hbm,
+            "note": "stable LSD radix sort (10-bit digits: two passes over a 20-bit cell key) plus the "
+                    "gather of the records; the sort's intermediate passes are not counted as algorithmic bytes"}
 
 
 def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, reps=3):
@@ -613,42 +645,81 @@ def sks_measure(torch, hs, n_c: int = 10, h: float = 0.01):
 
 
 def e2e(args, torch, hs, sr, w, prm, force_fn, launch, dev, ranks, pairs):
-    """Same step with inputs in pinned host memory, copies inside the timed region."""
+    """The step through the public API with inputs in pinned host memory: every
+    step copies its inputs (x, y, z, m, v) in and its results (v, FP64 moments)
+    out, inside the timed region.  Pipelined: a copy stream moves step k+1's
+    inputs and step k's results while step k computes (two device input
+    buffers); the serial variant (copies and compute on one stream) is
+    reported beside it."""
     host_in = torch.tensor(np.stack([w.x, w.y, w.z, w.m, w.vx, w.vy, w.vz]).astype(np.float32)).pin_memory()
     host_out = torch.empty((3, w.N), dtype=torch.float32).pin_memory()
     host_mom = torch.empty(9, dtype=torch.float64).pin_memory()
-    dbuf = torch.empty((7, w.N), dtype=torch.float32, device=dev)
+    dbuf = [torch.empty((7, w.N), dtype=torch.float32, device=dev) for _ in range(2)]
     a = torch.empty((3, w.N), dtype=torch.float32, device=dev)
+    mom = [torch.empty(9, dtype=torch.float64, device=dev) for _ in range(2)]
     stream = torch.cuda.current_stream()
+    copy = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    computed = torch.cuda.Event()
 
-    def step():
-        dbuf.copy_(host_in, non_blocking=True)
-        pos = dbuf[0:3]
-        m = dbuf[3]
-        v = dbuf[4:7]
+    def compute(b):
+        buf = dbuf[b]
+        pos, m, v = buf[0:3], buf[3], buf[4:7]
         sr.prepare(pos, m)
         force_fn(prm, a, launch=launch)
         sr.kick(v, a, w.dt)
-        mom = sr.moments(m, v, a)
-        host_out.copy_(v, non_blocking=True)
-        host_mom.copy_(mom, non_blocking=True)
+        mom[b].copy_(sr.moments(m, v, a))
 
-    for _ in range(max(1, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    ranks.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ranks.barrier()
-    t = ranks.max(e0.elapsed_time(e1))
+    def run_pipelined(K):
+        copy.wait_stream(stream)
+        with torch.cuda.stream(copy):
+            dbuf[0].copy_(host_in, non_blocking=True)
+            ready[0].record(copy)
+        for k in range(K):
+            b = k % 2
+            if k + 1 < K:  # next step's inputs, once the buffer's previous results have left
+                with torch.cuda.stream(copy):
+                    if k >= 1:
+                        copy.wait_event(freed[1 - b])
+                    dbuf[1 - b].copy_(host_in, non_blocking=True)
+                    ready[1 - b].record(copy)
+            stream.wait_event(ready[b])
+            compute(b)
+            computed.record(stream)
+            with torch.cuda.stream(copy):  # buffer b (inputs, v, moments) is next written by step k + 2,
+                copy.wait_event(computed)  # whose input copy follows this one on the copy stream
+                host_out.copy_(dbuf[b][4:7], non_blocking=True)
+                host_mom.copy_(mom[b], non_blocking=True)
+                freed[b].record(copy)
+        stream.wait_stream(copy)
+
+    def run_serial(K):
+        for _ in range(K):
+            dbuf[0].copy_(host_in, non_blocking=True)
+            compute(0)
+            host_out.copy_(dbuf[0][4:7], non_blocking=True)
+            host_mom.copy_(mom[0], non_blocking=True)
+
+    def timed(run):
+        run(max(1, args.warmup))
+        torch.cuda.synchronize()
+        ranks.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ranks.barrier()
+        return ranks.max(e0.elapsed_time(e1))
+
+    t = timed(run_pipelined)
+    t_serial = timed(run_serial)
     total = ranks.sum(float(pairs)) * args.steps
     return {"value": total / (t * 1e-3), "unit": UNIT, "ms_per_step": t / args.steps,
             "h2d_bytes_per_step": int(host_in.numel() * 4),
-            "d2h_bytes_per_step": int(host_out.numel() * 4 + host_mom.numel() * 8)}
+            "d2h_bytes_per_step": int(host_out.numel() * 4 + host_mom.numel() * 8),
+            "pipelined": True, "serial": {"value": total / (t_serial * 1e-3), "ms_per_step": t_serial / args.steps}}
 
 
 def check_sample(sr, pos, m, prm, w, force_fn, launch, S=256):

@@ -13,7 +13,7 @@ namespace hacc {
 namespace {
 
 constexpr int KEY_THREADS = 256;
-constexpr int RADIX_BITS = 8;
+constexpr int RADIX_BITS = 10;  // 1024 digits: a 20-bit cell key sorts in two passes
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int R_THREADS = 256;
 constexpr int R_WARPS = R_THREADS / 32;
@@ -90,7 +90,10 @@ k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *
         keys[i] = key;
         r.w = m[i];
         rec[i] = r;
-        atomicAdd(&counts[key], 1);
+        // one atomic per distinct cell of the warp: consecutive particles of a halo share cells
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, key);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
     }
 }
 

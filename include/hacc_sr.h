@@ -107,7 +107,9 @@ typedef struct hacc_lists {
     int32_t *task_order; /* [task_cap] the order the pair kernels take tasks in: by descending
                             cost class (particles x list length, power-of-two classes), stable */
     int64_t task_cap;  /* capacity of `tasks`, in tasks */
-    int32_t split_T;   /* a task holds at most split_T particles of one cell */
+    int32_t split_T;   /* a task holds at most split_T particles of one cell; the pair calls take
+                          1..128 (one, two or four i particles per lane in the symmetric force
+                          kernel; the other pair kernels walk a task in 64-particle sub-chunks) */
     int32_t pad;
 } hacc_lists;
 

@@ -100,10 +100,11 @@ def tune(run, config: str, mode: str = "force", quick: bool = False, reps: int =
     return best[0], table
 
 
-def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str = CACHE) -> dict:
-    """Tune split threshold and launch shape of the force kernel, then the
-    launch shapes of the adjoint and the symmetric force kernel on the chosen
-    lists, for one of the standard workloads (synth.make_config names)."""
+def tune_workload(config: str, splits=(32, 64, 128), quick: bool = False, path: str = CACHE) -> dict:
+    """Tune one of the standard workloads (synth.make_config names): the split
+    threshold by the symmetric force kernel (the step's force), then, on those
+    lists, the launch shapes of the symmetric and gather force kernels and of
+    both adjoints."""
     import numpy as np
     import torch
 
@@ -115,30 +116,32 @@ def tune_workload(config: str, splits=(32, 64), quick: bool = False, path: str =
     prm = SRParams(w.eps, w.rcut, default_coeffs(w.rcut, w.eps))
     pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
     m = torch.tensor(w.m, device="cuda")
+    out = torch.empty((3, w.N), device="cuda")
     best = None
     report = {}
     for T in splits:
         sr = ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
         sr.prepare(pos, m)
-        out = torch.empty((3, w.N), device="cuda")
-        L, table = tune(lambda L: sr.force(prm, out, launch=L), config, quick=quick, write=False)
+        _, table = tune(lambda L: sr.force_symmetric(prm, out, launch=L), config, quick=True, write=False)
         ms = min(t[1] for t in table if t[1] is not None)
         report[T] = [(t[0].__dict__, t[1]) for t in table]
-        if best is None or ms < best[2]:
-            best = (T, L, ms, sr)
+        if best is None or ms < best[1]:
+            best = (T, ms)
         del sr
         torch.cuda.empty_cache()
-    T, L, ms, sr = best
+    T = best[0]
+    sr = ShortRange(w.L, w.vol_off, w.rcut, cell_min=w.cell_min, split_T=T)
+    sr.prepare(pos, m)
     cache = load_cache(path)
     ent = cache.setdefault(_key(config), {})
-    ent["force"] = {"launch": L.__dict__, "ms": ms, "split_T": T}
+    Ls, tab_s = tune(lambda L: sr.force_symmetric(prm, out, launch=L), config, quick=quick, write=False)
+    ent["symmetric"] = {"launch": Ls.__dict__, "ms": min(t[1] for t in tab_s if t[1] is not None)}
+    L, tab = tune(lambda L: sr.force(prm, out, launch=L), config, quick=quick, write=False)
+    ent["force"] = {"launch": L.__dict__, "ms": min(t[1] for t in tab if t[1] is not None), "split_T": T}
     lam = torch.randn((3, w.N), device="cuda")
     La, _ = tune(lambda L: sr.adjoint(prm, lam, want_gm=False, launch=L), config, mode="adjoint", quick=True,
                  write=False)
     ent["adjoint"] = {"launch": La.__dict__}
-    Ls, tab_s = tune(lambda L: sr.force_symmetric(prm, out, launch=L), config, mode="symmetric", quick=quick,
-                     write=False)
-    ent["symmetric"] = {"launch": Ls.__dict__, "ms": min(t[1] for t in tab_s if t[1] is not None)}
     # 128 registers per thread: at most 16 warps per SM
     cands = [c for c in candidates(quick) if c.warps_per_cta * c.ctas_per_sm <= 16]
     Lsa, tab_sa = tune(lambda L: sr.adjoint_symmetric(prm, lam, want_gm=False, launch=L), config,

@@ -389,11 +389,14 @@ __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
         if (t >= ntask) break;
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
-        bool ok;
-        if (task.z - task.y > 32)
-            ok = run_task<MODE, JT, STAGES, 2>(a, ring, comp, lane, task.x, task.y, task.z, vol);
-        else
-            ok = run_task<MODE, JT, STAGES, 1>(a, ring, comp, lane, task.x, task.y, task.z, vol);
+        bool ok = true;
+        for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
+            const int se = min(sb + 64, task.z);
+            if (se - sb > 32)
+                ok = run_task<MODE, JT, STAGES, 2>(a, ring, comp, lane, task.x, sb, se, vol);
+            else
+                ok = run_task<MODE, JT, STAGES, 1>(a, ring, comp, lane, task.x, sb, se, vol);
+        }
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();

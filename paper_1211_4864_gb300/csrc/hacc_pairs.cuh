@@ -327,7 +327,9 @@ int check_common(const hacc_mesh *mesh, const hacc_binned *b, const hacc_lists *
     if (!l->nbr_off || !l->n_tasks || (mesh->n_entries > 0 && (!l->nbr_cell || !l->nbr_shift)))
         return HACC_ERR_INVALID;
     if (!l->tasks || !aligned16(l->tasks) || !l->task_order) return HACC_ERR_INVALID;
-    if (l->split_T < 1 || l->split_T > 64) return HACC_ERR_INVALID;  // at most two i particles per lane
+    // tasks above 64 particles: the gather kernels and the adjoints walk them in 64-particle
+    // sub-chunks, the symmetric force kernel holds four i particles per lane
+    if (l->split_T < 1 || l->split_T > 128) return HACC_ERR_INVALID;
     if (launch) {
         if (launch->warps_per_cta < 1 || launch->warps_per_cta > 8 || launch->ctas_per_sm < 1 ||
             launch->ctas_per_sm > 8)

@@ -152,15 +152,37 @@ __device__ __forceinline__ void flush_j(const JRec &J, double *acc, int64_t N)
     atomicAdd(acc + 2 * N + J.slot, (double)J.fz);
 }
 
+// i sums of a task: float32 within a staged tile, folded into a compensated
+// (hi, lo) pair per component across tiles.  One or two i per lane keep the
+// pairs in registers; four i per lane keep them in shared memory
+// (comp[((u * 3 + k) * 2 + {0, 1}) * 32 + lane]) to stay within 80 registers.
+constexpr int SYM_IPL_MAX = 4;
+constexpr int SYM_COMP_BYTES = SYM_IPL_MAX * 3 * 2 * 32 * 4;
+
 template <int IPL>
 struct AccI {
-    float a[IPL][3], h[IPL][3], l[IPL][3];
-    __device__ __forceinline__ AccI()
+    static constexpr bool SMEM = IPL > 2;
+    float a[IPL][3];
+    float h[SMEM ? 1 : IPL][3], l[SMEM ? 1 : IPL][3];
+    float *comp;
+    int lane;
+    __device__ __forceinline__ float &chi(int u, int k) const { return comp[((u * 3 + k) * 2 + 0) * 32 + lane]; }
+    __device__ __forceinline__ float &clo(int u, int k) const { return comp[((u * 3 + k) * 2 + 1) * 32 + lane]; }
+    __device__ __forceinline__ AccI(float *c, int ln) : comp(c), lane(ln)
     {
 #pragma unroll
         for (int u = 0; u < IPL; ++u)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) a[u][k] = h[u][k] = l[u][k] = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                a[u][k] = 0.f;
+                if constexpr (SMEM) {
+                    chi(u, k) = 0.f;
+                    clo(u, k) = 0.f;
+                } else {
+                    h[u][k] = 0.f;
+                    l[u][k] = 0.f;
+                }
+            }
     }
     __device__ __forceinline__ void fold()
     {
@@ -168,17 +190,44 @@ struct AccI {
         for (int u = 0; u < IPL; ++u)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                two_sum_acc(h[u][k], l[u][k], a[u][k]);
+                if constexpr (SMEM) {
+                    float hh = chi(u, k), ll = clo(u, k);
+                    two_sum_acc(hh, ll, a[u][k]);
+                    chi(u, k) = hh;
+                    clo(u, k) = ll;
+                } else {
+                    two_sum_acc(h[u][k], l[u][k], a[u][k]);
+                }
                 a[u][k] = 0.f;
             }
     }
+    // the compensated total as a float64
+    __device__ __forceinline__ double total(int u, int k) const
+    {
+        if constexpr (SMEM)
+            return (double)chi(u, k) + (double)clo(u, k);
+        else
+            return (double)h[u][k] + (double)l[u][k];
+    }
 };
+
+// The chunk against itself, block B: its i set B held as j.  Set B meets it
+// above the diagonal (j > i), sets below B meet all of it, sets above none.
+template <int IPL, int B>
+__device__ __forceinline__ void diag_block(const float4 (&oi)[IPL], const bool (&active)[IPL], int ib,
+                                           const PairConsts &K, AccI<IPL> &A, double *acc, int64_t N, int lane)
+{
+    constexpr unsigned SKIP = ((1u << IPL) - 1u) & ~((2u << B) - 1u);
+    JRec J{oi[B].x, oi[B].y, oi[B].z, oi[B].w, 0.f, 0.f, 0.f, active[B] ? ib + 32 * B + lane : -1};
+    rotate_block<IPL, (1u << B), SKIP>(J, oi, K, A.a, lane);
+    flush_j(J, acc, N);
+}
 
 // One task: i particles [ib, ie) of cell c against their own chunk (j > i),
 // the rest of the cell, and the forward half of the cell's list.
 template <int JT, int STAGES, int IPL>
-__device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STAGES> &ring, double *acc, int64_t N,
-                                             int lane, int c, int ib, int ie, const hacc_volume &vol)
+__device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STAGES> &ring, float *comp, double *acc,
+                                             int64_t N, int lane, int c, int ib, int ie, const hacc_volume &vol)
 {
     const PairConsts &K = a.k;
     const int n = vol.n;
@@ -194,20 +243,16 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
         active[u] = i < ie;
         oi[u] = active[u] ? a.pos[i] : make_float4(FAR, FAR, FAR, 0.f);
     }
-    AccI<IPL> A;
+    AccI<IPL> A(comp, lane);
 
-    // the chunk against itself: block u holds the chunk's i set u as j
-    {
-        JRec J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, 0.f, 0.f, 0.f, active[0] ? ib + lane : -1};
-        rotate_block<IPL, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, K, A.a, lane);
-        flush_j(J, acc, N);
-        if constexpr (IPL == 2) {
-            JRec J1{oi[1].x, oi[1].y, oi[1].z, oi[1].w, 0.f, 0.f, 0.f, active[1] ? ib + 32 + lane : -1};
-            rotate_block<IPL, 2u, 0u>(J1, oi, K, A.a, lane);
-            flush_j(J1, acc, N);
-        }
-        A.fold();
+    // the chunk against itself: block B holds the chunk's i set B as j
+    diag_block<IPL, 0>(oi, active, ib, K, A, acc, N, lane);
+    if constexpr (IPL > 1) diag_block<IPL, 1>(oi, active, ib, K, A, acc, N, lane);
+    if constexpr (IPL > 2) {
+        diag_block<IPL, 2>(oi, active, ib, K, A, acc, N, lane);
+        diag_block<IPL, 3>(oi, active, ib, K, A, acc, N, lane);
     }
+    A.fold();
 
     // the cell after the chunk, then the forward entries (staged)
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
@@ -291,24 +336,32 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
     for (int u = 0; u < IPL; ++u) {
         if (!active[u]) continue;
         const int i = ib + lane + 32 * u;
-        atomicAdd(acc + i, (double)A.h[u][0] + (double)A.l[u][0]);
-        atomicAdd(acc + N + i, (double)A.h[u][1] + (double)A.l[u][1]);
-        atomicAdd(acc + 2 * N + i, (double)A.h[u][2] + (double)A.l[u][2]);
+        atomicAdd(acc + i, A.total(u, 0));
+        atomicAdd(acc + N + i, A.total(u, 1));
+        atomicAdd(acc + 2 * N + i, A.total(u, 2));
     }
     return true;
+}
+
+// Shared memory of one warp of the symmetric force kernel: the staged tiles,
+// the compensated i sums of four-i tasks, the mbarriers; 128-B aligned.
+__host__ __device__ constexpr int sym_warp_smem_bytes(int jt, int stages)
+{
+    return (warp_tiles_bytes(FORCE, jt, stages) + SYM_COMP_BYTES + stages * 8 + 127) / 128 * 128;
 }
 
 template <int JT, int STAGES>
 __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc, int64_t N)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int WARP_BYTES = warp_smem_bytes(FORCE, JT, STAGES);
+    constexpr int WARP_BYTES = sym_warp_smem_bytes(JT, STAGES);
     constexpr int TILE_BYTES = warp_tiles_bytes(FORCE, JT, STAGES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + (size_t)warp * WARP_BYTES;
     Ring<FORCE, JT, STAGES> ring;
     ring.tiles = reinterpret_cast<float4 *>(wbase);
-    ring.bars = reinterpret_cast<uint64_t *>(wbase + TILE_BYTES);
+    float *comp = reinterpret_cast<float *>(wbase + TILE_BYTES);
+    ring.bars = reinterpret_cast<uint64_t *>(wbase + TILE_BYTES + SYM_COMP_BYTES);
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&ring.bars[s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -324,10 +377,13 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
         bool ok;
-        if (task.z - task.y > 32)
-            ok = run_task_sym<JT, STAGES, 2>(a, ring, acc, N, lane, task.x, task.y, task.z, vol);
+        const int size = task.z - task.y;
+        if (size > 64)
+            ok = run_task_sym<JT, STAGES, 4>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+        else if (size > 32)
+            ok = run_task_sym<JT, STAGES, 2>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         else
-            ok = run_task_sym<JT, STAGES, 1>(a, ring, acc, N, lane, task.x, task.y, task.z, vol);
+            ok = run_task_sym<JT, STAGES, 1>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();
@@ -352,7 +408,7 @@ k_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restric
 template <int JT, int STAGES>
 int launch_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
 {
-    const size_t smem = (size_t)warps * warp_smem_bytes(FORCE, JT, STAGES);
+    const size_t smem = (size_t)warps * sym_warp_smem_bytes(JT, STAGES);
     auto kern = k_pairs_sym<JT, STAGES>;
     if (smem > 48 * 1024)
         HACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -639,11 +695,14 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
         if (t >= ntask) break;
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
-        bool ok;
-        if (task.z - task.y > 32)
-            ok = run_task_adj_sym<JT, STAGES, 2, GM>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
-        else
-            ok = run_task_adj_sym<JT, STAGES, 1, GM>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+        bool ok = true;
+        for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
+            const int se = min(sb + 64, task.z);
+            if (se - sb > 32)
+                ok = run_task_adj_sym<JT, STAGES, 2, GM>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
+            else
+                ok = run_task_adj_sym<JT, STAGES, 1, GM>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
+        }
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();

@@ -51,7 +51,8 @@ def oracle_force(w: Workload, v=0, targets=None):
     return oracle.sr_force(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), EPS, RC, c, targets)
 
 
-@pytest.mark.parametrize("case", ["uniform", "clustered", "fine_mesh", "small_box", "tiny_tasks"])
+@pytest.mark.parametrize("case", ["uniform", "clustered", "fine_mesh", "small_box", "tiny_tasks", "tasks128",
+                                  "tasks100"])
 def test_symmetric_against_oracle_and_gather(hs, case):
     cell_min, split_T = None, 64
     if case == "uniform":
@@ -62,8 +63,12 @@ def test_symmetric_against_oracle_and_gather(hs, case):
         w, cell_min = uniform_box(3000, 14.0, seed=18), 1.5
     elif case == "small_box":  # n = 3 cells per side: every neighbour is a periodic image
         w = uniform_box(1500, 9.0, seed=19)
-    else:  # chunks of 7 particles: many tasks per cell, every diagonal block ragged
+    elif case == "tiny_tasks":  # chunks of 7 particles: many tasks per cell, every diagonal block ragged
         w, split_T = clustered_box(16, 3, seed=22), 7
+    elif case == "tasks128":  # four i per lane in the symmetric kernel, 64-particle sub-chunks in the gather
+        w, split_T = clustered_box(20, 4, seed=25), 128
+    else:  # 100-particle chunks: the fourth i set partly empty
+        w, split_T = clustered_box(20, 4, seed=26), 100
     rng = np.random.default_rng(5)
     w.m[:] = rng.uniform(0.5, 1.5, w.N).astype(np.float32)
     sr, a_s, a_g, mom = run_both(hs, w, cell_min=cell_min, split_T=split_T)
@@ -149,7 +154,7 @@ def test_symmetric_on_tree_lists(hs, case, leaf_max):
 
 
 @pytest.mark.parametrize("case,want_gm", [("uniform", True), ("clustered", True), ("clustered", False),
-                                          ("fine_mesh", True), ("tiny_tasks", True)])
+                                          ("fine_mesh", True), ("tiny_tasks", True), ("tasks128", True)])
 def test_symmetric_adjoint_against_oracle_and_gather(hs, case, want_gm):
     import torch
     cell_min, split_T = None, 64
@@ -159,6 +164,8 @@ def test_symmetric_adjoint_against_oracle_and_gather(hs, case, want_gm):
         w = clustered_box(20, 4, seed=21)
     elif case == "fine_mesh":
         w, cell_min = uniform_box(3000, 14.0, seed=18), 1.5
+    elif case == "tasks128":  # both adjoints walk 128-particle tasks in 64-particle sub-chunks
+        w, split_T = clustered_box(20, 4, seed=25), 128
     else:
         w, split_T = clustered_box(16, 3, seed=22), 7
     rng = np.random.default_rng(9)

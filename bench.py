@@ -40,12 +40,12 @@ FLOPS_PER_SYM_PAIR = 36
 # ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
 # they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2133427712 + 953597952,
+    "gather": {"workload": "clustered256", "bytes": 2242479872 + 969879296,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "718e24bc8f68bb0827cfae2c79daa0e94fcba58b0665c240da026706163e1b70"},
-    "symmetric": {"workload": "clustered256", "bytes": 2695881728 + 1420933888,
+               "sha256": "d744c9399634f0772f610da413d65a764cab4258a87199d33e269e4aa327c753"},
+    "symmetric": {"workload": "clustered256", "bytes": 2829236736 + 1512726272,
                   "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
-                  "sha256": "d9ace8e4d55d7b2deba115a8720bdffe75b14da975097fc08409644e39b26cce"},
+                  "sha256": "092ff2768bbc88e8b87096c70dc1ed8eebcf9dced40d91cb30667a53e57fe8d5"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

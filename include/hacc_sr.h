@@ -132,6 +132,12 @@ typedef struct hacc_launch {
 /* Library version and build target, e.g. "hacc_sr 1 sm_103a". Host. */
 const char *hacc_version(void);
 
+/* Reads the device status word `status` into the host word *value once the
+ * work enqueued on `stream` so far has finished (synchronises `stream`).
+ * HACC_ERR_CUDA if the copy or the wait fails (a fault of earlier work shows
+ * here). */
+int hacc_get_status(const uint32_t *status, uint32_t *value, void *stream);
+
 /* Number of kernels this library has launched in this process so far (host;
  * a tracing aid: the difference across a region counts its launches). */
 uint64_t hacc_kernel_launches(void);

@@ -76,6 +76,7 @@ _PS = ctypes.POINTER
 # name -> (restype, argtypes); the order of the header
 SIGNATURES = {
     "hacc_version": (ctypes.c_char_p, []),
+    "hacc_get_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32), _P]),
     "hacc_kernel_launches": (ctypes.c_uint64, []),
     "hacc_mesh_plan": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_float, ctypes.c_float,
                                       _PS(hacc_volume), _PS(hacc_mesh)]),

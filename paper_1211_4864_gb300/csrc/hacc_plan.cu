@@ -6,6 +6,15 @@
 
 extern "C" const char *hacc_version(void) { return "hacc_sr 1 sm_103a"; }
 
+extern "C" int hacc_get_status(const uint32_t *status, uint32_t *value, void *stream)
+{
+    if (!status || !value) return HACC_ERR_INVALID;
+    cudaStream_t st = hacc::as_stream(stream);
+    HACC_CUDA_TRY(cudaMemcpyAsync(value, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    HACC_CUDA_TRY(cudaStreamSynchronize(st));
+    return HACC_OK;
+}
+
 extern "C" int hacc_mesh_plan(int32_t V, const float *L, const int64_t *vol_off, float cell_min,
                               float rcut, hacc_volume *table, hacc_mesh *out_mesh)
 {

@@ -77,6 +77,14 @@ def hacc_version() -> str:
     return _lib.load().hacc_version().decode()
 
 
+def hacc_get_status(status) -> int:
+    """The device status word `status` (a CUDA int32 tensor of one element),
+    once the current stream has finished its enqueued work."""
+    v = ctypes.c_uint32()
+    check(_lib.load().hacc_get_status(_ptr(status), ctypes.byref(v), _stream()), "hacc_get_status")
+    return int(v.value)
+
+
 def hacc_kernel_launches() -> int:
     return int(_lib.load().hacc_kernel_launches())
 
@@ -408,7 +416,7 @@ class ShortRange:
         self.build_lists()
 
     def check_status(self):
-        s = int(self.status.item())
+        s = hacc_get_status(self.status)
         if s:
             self.status.zero_()
             raise HaccError(f"device status {s:#x}")

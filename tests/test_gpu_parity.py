@@ -319,8 +319,12 @@ def test_nonfinite_position_flagged(torch, hs):
     sr = hs.ShortRange(w.L, w.vol_off, RC)
     pos, m = to_dev(torch, w)
     sr.prepare(pos, m)
+    # the library's own status read (waits for the stream) agrees with a plain tensor read
+    assert hs.hacc_get_status(sr.status) & 4
     torch.cuda.synchronize()
     assert int(sr.status.item()) & 4
+    with pytest.raises(hs.HaccError):
+        sr.check_status()
 
 
 # --------------------------------------------------------------------------

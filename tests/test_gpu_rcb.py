@@ -223,3 +223,21 @@ def test_rebuild_on_moved_particles_is_reproducible(torch, hs):
     sr.check_status()
     assert torch.equal(first[0], sr.perm) and torch.equal(first[1], sr.sorted4)
     assert torch.equal(first[2], sr.nbr_cell[:sr.n_entries])
+
+
+def test_tree_capacity_overflow_is_flagged_not_written_past(torch, hs):
+    """A leaf capacity far below the leaf count: the build flags
+    HACC_STATUS_CAPACITY, writes nothing past the arrays, and prepare()
+    raises before any walk of the incomplete tree."""
+    w = uniform_box(3000, 14.0, seed=13)
+    sr = hs.ShortRange(w.L, w.vol_off, RC, builder="rcb", leaf_max=8)
+    sentinel = torch.full((64,), -7, dtype=torch.int32, device="cuda")
+    sr.leaf_start = torch.cat([sr.leaf_start[:11], sentinel])  # room for 10 leaves, then a guard band
+    sr.tree.leaf_start = sr.leaf_start.data_ptr()
+    sr.tree.leaf_cap = 10
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    with pytest.raises(hs.HaccError):
+        sr.prepare(pos, torch.tensor(w.m, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(sr.leaf_start[11:], sentinel)
+    assert int(sr.n_leaves.item()) == 10

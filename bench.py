@@ -811,7 +811,8 @@ def sweep(args):
     GPU analogue of the paper's threading study (Fig. 5: kernel performance vs
     ranks x threads per node and neighbour-list size 500-2500).  Uniform boxes
     of side 96 at densities 0.6-3 particles per grid cell cubed give 440-2200
-    candidate neighbours per particle with r_c = 3."""
+    candidate neighbours per particle with r_c = 3; both pair kernels, split
+    thresholds 32-128, 1-3 resident CTAs of 8 warps per SM."""
     import torch
 
     import paper_1211_4864_gb300 as hs
@@ -826,26 +827,29 @@ def sweep(args):
         w = uniform_box(n, 96.0, seed=90)
         pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
         m = torch.tensor(w.m, device="cuda")
-        for T in (32, 64):
+        for T in (32, 64, 128):
             sr = hs.ShortRange(w.L, w.vol_off, 3.0, split_T=T)
             sr.prepare(pos, m)
             torch.cuda.synchronize()
             pairs = sr.pair_count()
             out = torch.empty((3, n), device="cuda")
-            for cps in (1, 2, 3):
-                L = hs.Launch(8, cps, 128, 2)
-                sr.force(prm, out, launch=L)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(5):
-                    sr.force(prm, out, launch=L)
-                e1.record()
-                torch.cuda.synchronize()
-                t = e0.elapsed_time(e1) / 5
-                rows.append({"density": rho, "list_length": pairs / n, "split_T": T, "ctas_per_sm": cps,
-                             "warps_per_sm": 8 * cps, "ms": t, "pairs_per_s": pairs / (t * 1e-3),
-                             "frac_fp32_peak": FLOPS_PER_PAIR * pairs / (t * 1e-3) / peak})
+            for kernel, fn, flops in (("gather", sr.force, FLOPS_PER_PAIR * pairs),
+                                      ("symmetric", sr.force_symmetric, FLOPS_PER_SYM_PAIR * pairs / 2)):
+                for cps in (1, 2, 3):
+                    L = hs.Launch(8, cps, 128, 2)
+                    fn(prm, out, launch=L)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(5):
+                        fn(prm, out, launch=L)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    t = e0.elapsed_time(e1) / 5
+                    rows.append({"density": rho, "list_length": pairs / n, "split_T": T, "kernel": kernel,
+                                 "ctas_per_sm": cps, "warps_per_sm": 8 * cps, "ms": t,
+                                 "interactions_per_s": pairs / (t * 1e-3),
+                                 "frac_fp32_peak_executed": flops / (t * 1e-3) / peak})
             sr.check_status()
             del sr
             torch.cuda.empty_cache()

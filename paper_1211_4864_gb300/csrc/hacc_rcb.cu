@@ -5,9 +5,9 @@
 //
 // Build, level-synchronous.  All groups still to be split at one depth are
 // processed together.  Their particles are cut into chunks of CHUNK slots (a
-// chunk never spans two groups).  Per chunk one CTA reduces the integer box and
-// the coordinate sums into the group's statistics (integer atomics: exact and
-// order-free); a second pass counts the particles that go left; a global scan
+// chunk never spans two groups).  Per chunk one warp reduces the integer box
+// and the coordinate sums into the group's statistics (integer atomics: exact
+// and order-free); a second pass counts the particles that go left; a global scan
 // over the chunks turns the counts into stable destinations; the scatter then
 // writes every particle to the next level's buffer, or straight to the final
 // buffer when its half is a leaf.  Halves that still need splitting become
@@ -27,9 +27,8 @@ namespace hacc {
 namespace {
 
 constexpr int QBITS = HACC_RCB_QBITS;
-constexpr int CHUNK = 2048;       // slots per chunk
-constexpr int CT = 256;           // threads of a chunk CTA
-constexpr int IPT = CHUNK / CT;   // consecutive slots per thread in the scatter
+constexpr int CHUNK = 256;        // slots per chunk; one warp per chunk
+constexpr int IPT = CHUNK / 32;   // consecutive slots per lane in the scatter
 constexpr int STACK = HACC_RCB_MAX_DEPTH + 2;
 constexpr int32_t EMPTY_ROOT = INT_MIN;
 
@@ -185,24 +184,34 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
     return v;
 }
 
-// Per chunk: integer box and coordinate sums, merged into the group by atomics.
-__global__ void __launch_bounds__(CT)
-k_rcb_reduce(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, const int32_t *__restrict__ chunk_base,
-             int64_t Smax, const int4 *__restrict__ qa, GroupStat *__restrict__ stat)
+// Group of every chunk of the level (the last s < S with chunk_base[s] <= c).
+__global__ void __launch_bounds__(256)
+k_rcb_chunk_map(const int32_t *__restrict__ S_in, const int32_t *__restrict__ chunk_base, int64_t Smax,
+                int32_t *__restrict__ chunk_group)
 {
-    __shared__ int s_lo[CT / 32][3], s_hi[CT / 32][3];
-    __shared__ unsigned long long s_sum[CT / 32][3];
     const int S = *S_in;
     const int total = chunk_base[Smax];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = blockIdx.x; c < total; c += gridDim.x) {
-        const int s = group_of_chunk(chunk_base, S, c);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x)
+        chunk_group[c] = group_of_chunk(chunk_base, S, c);
+}
+
+// Per chunk (one warp): integer box and coordinate sums, merged into the group by atomics.
+__global__ void __launch_bounds__(256)
+k_rcb_reduce(const int4 *__restrict__ grp, const int32_t *__restrict__ chunk_base,
+             const int32_t *__restrict__ chunk_group, int64_t Smax, const int4 *__restrict__ qa,
+             GroupStat *__restrict__ stat)
+{
+    const int total = chunk_base[Smax];
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < total; c += warps) {
+        const int s = chunk_group[c];
         const int4 g = grp[s];
         const int p0 = g.x + (c - chunk_base[s]) * CHUNK;
         const int p1 = min(g.y, p0 + CHUNK);
         int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
         unsigned long long sm[3] = {0ull, 0ull, 0ull};
-        for (int p = p0 + threadIdx.x; p < p1; p += CT) {
+        for (int p = p0 + lane; p < p1; p += 32) {
             const int4 q = qa[p];
             const int v[3] = {q.x, q.y, q.z};
 #pragma unroll
@@ -218,92 +227,51 @@ k_rcb_reduce(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, con
             hi[a] = warp_max(hi[a]);
             sm[a] = warp_sum64(sm[a]);
         }
-        if (lane == 0) {
-            for (int a = 0; a < 3; ++a) {
-                s_lo[warp][a] = lo[a];
-                s_hi[warp][a] = hi[a];
-                s_sum[warp][a] = sm[a];
-            }
+        if (lane < 3) {
+            const int a = lane;
+            atomicMin(&stat[s].lo[a], a == 0 ? lo[0] : (a == 1 ? lo[1] : lo[2]));
+            atomicMax(&stat[s].hi[a], a == 0 ? hi[0] : (a == 1 ? hi[1] : hi[2]));
+            atomicAdd(&stat[s].sum[a], a == 0 ? sm[0] : (a == 1 ? sm[1] : sm[2]));
         }
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            const int a = threadIdx.x;
-            int l = INT_MAX, h = -1;
-            unsigned long long t = 0ull;
-            for (int w = 0; w < CT / 32; ++w) {
-                l = min(l, s_lo[w][a]);
-                h = max(h, s_hi[w][a]);
-                t += s_sum[w][a];
-            }
-            atomicMin(&stat[s].lo[a], l);
-            atomicMax(&stat[s].hi[a], h);
-            atomicAdd(&stat[s].sum[a], t);
-        }
-        __syncthreads();
     }
 }
 
-// Per chunk: how many of its particles go left.
-__global__ void __launch_bounds__(CT)
-k_rcb_count(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, const int32_t *__restrict__ chunk_base,
-            int64_t Smax, const int4 *__restrict__ qa, const GroupStat *__restrict__ stat,
-            int32_t *__restrict__ chunk_left)
+// Per chunk (one warp): how many of its particles go left.
+__global__ void __launch_bounds__(256)
+k_rcb_count(const int4 *__restrict__ grp, const int32_t *__restrict__ chunk_base,
+            const int32_t *__restrict__ chunk_group, int64_t Smax, const int4 *__restrict__ qa,
+            const GroupStat *__restrict__ stat, int32_t *__restrict__ chunk_left)
 {
-    __shared__ int s_cnt[CT / 32];
-    const int S = *S_in;
     const int total = chunk_base[Smax];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = blockIdx.x; c < total; c += gridDim.x) {
-        const int s = group_of_chunk(chunk_base, S, c);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < total; c += warps) {
+        const int s = chunk_group[c];
         const int4 g = grp[s];
         const int cnt = g.y - g.x;
         const Split sp = decide(stat[s], cnt);
         const int p0 = g.x + (c - chunk_base[s]) * CHUNK;
         const int p1 = min(g.y, p0 + CHUNK);
         int n = 0;
-        for (int p = p0 + threadIdx.x; p < p1; p += CT) n += goes_left(sp, qa[p], p - g.x, cnt) ? 1 : 0;
+        for (int p = p0 + lane; p < p1; p += 32) n += goes_left(sp, qa[p], p - g.x, cnt) ? 1 : 0;
         n = __reduce_add_sync(0xffffffffu, n);
-        if (lane == 0) s_cnt[warp] = n;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < CT / 32; ++w) t += s_cnt[w];
-            chunk_left[c] = t;
-        }
-        __syncthreads();
+        if (lane == 0) chunk_left[c] = n;
     }
 }
 
-// Block-wide exclusive scan of one int per thread (CT threads).
-__device__ __forceinline__ int block_excl_scan(int v, int *s_warp)
+// Per chunk (one warp, IPT consecutive slots per lane): stable destinations;
+// halves that are leaves go to the final buffer.
+__global__ void __launch_bounds__(256)
+k_rcb_scatter(const int4 *__restrict__ grp, const int32_t *__restrict__ chunk_base,
+              const int32_t *__restrict__ chunk_group, const int32_t *__restrict__ chunk_loff, int64_t Smax,
+              const int4 *__restrict__ qa, const GroupStat *__restrict__ stat, int leaf_max, int max_depth,
+              int4 *__restrict__ qb, int4 *__restrict__ fin)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += s_warp[w];
-    __syncthreads();
-    return base + incl - v;
-}
-
-// Per chunk: stable destinations; halves that are leaves go to the final buffer.
-__global__ void __launch_bounds__(CT)
-k_rcb_scatter(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, const int32_t *__restrict__ chunk_base,
-              const int32_t *__restrict__ chunk_loff, int64_t Smax, const int4 *__restrict__ qa,
-              const GroupStat *__restrict__ stat, int leaf_max, int max_depth, int4 *__restrict__ qb,
-              int4 *__restrict__ fin)
-{
-    __shared__ int s_warp[CT / 32];
-    const int S = *S_in;
     const int total = chunk_base[Smax];
-    for (int c = blockIdx.x; c < total; c += gridDim.x) {
-        const int s = group_of_chunk(chunk_base, S, c);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < total; c += warps) {
+        const int s = chunk_group[c];
         const int4 g = grp[s];
         const int cnt = g.y - g.x;
         const Split sp = decide(stat[s], cnt);
@@ -314,7 +282,7 @@ k_rcb_scatter(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, co
         const int p1 = min(g.y, p0 + CHUNK);
         const bool leaf_l = is_leaf(nl, g.w + 1, leaf_max, max_depth);
         const bool leaf_r = is_leaf(cnt - nl, g.w + 1, leaf_max, max_depth);
-        const int r0 = threadIdx.x * IPT;  // this thread's slots p0 + r0 .. + IPT - 1
+        const int r0 = lane * IPT;  // this lane's slots p0 + r0 .. + IPT - 1
         int4 q[IPT];
         unsigned flags = 0;
         int n = 0;
@@ -329,18 +297,24 @@ k_rcb_scatter(const int4 *__restrict__ grp, const int32_t *__restrict__ S_in, co
                 }
             }
         }
-        int left_before = block_excl_scan(n, s_warp);  // left slots of this chunk before r0
+        int incl = n;  // exclusive warp scan of the lanes' left counts: left slots of the chunk before r0
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int left_before = incl - n;
+        const int rb = (p0 - g.x) - lb;  // right particles of the group before this chunk
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const int p = p0 + r0 + j;
             if (p >= p1) break;
-            const int r = (p - p0);  // slot within the chunk
+            const int r = p - p0;  // slot within the chunk
             if (flags & (1u << j)) {
                 const int dst = g.x + lb + left_before;
                 if (leaf_l) fin[dst] = q[j]; else qb[dst] = q[j];
                 ++left_before;
             } else {
-                const int rb = (p0 - g.x) - lb;  // right particles of the group before this chunk
                 const int dst = g.x + nl + rb + (r - left_before);
                 if (leaf_r) fin[dst] = q[j]; else qb[dst] = q[j];
             }
@@ -744,7 +718,8 @@ struct Carver {
 
 struct BuildWs {
     int4 *qa, *qb, *fin, *grp0, *grp1;
-    int32_t *head, *leaf_of_pos, *nchunk, *chunk_base, *kids, *kid_off, *chunk_left, *chunk_loff, *S, *lvl_base;
+    int32_t *head, *leaf_of_pos, *nchunk, *chunk_base, *kids, *kid_off, *chunk_left, *chunk_loff, *chunk_group, *S,
+        *lvl_base;
     GroupStat *stat;
     char *scan_ws;
     int64_t Smax, Cmax;
@@ -772,6 +747,7 @@ BuildWs build_layout(int64_t N, int leaf_max, void *ws)
     B.kid_off = c.take<int32_t>(B.Smax + 1);
     B.chunk_left = c.take<int32_t>(B.Cmax);
     B.chunk_loff = c.take<int32_t>(B.Cmax + 1);
+    B.chunk_group = c.take<int32_t>(B.Cmax);
     B.S = c.take<int32_t>(2);
     B.lvl_base = c.take<int32_t>(HACC_RCB_MAX_DEPTH + 2);
     int64_t ns = (int64_t)n1;
@@ -864,7 +840,7 @@ extern "C" int hacc_rcb_build(const hacc_mesh *mesh, const float *x, const float
     int4 *qa = B.qa, *qb = B.qb, *grp = B.grp0, *grp_next = B.grp1;
     int32_t *S_in = &B.S[0], *S_out = &B.S[1];
     const int gs = grid_for(B.Smax, 16);
-    const int gc = num_sms() * 8;  // chunk kernels: persistent over the level's chunks
+    const int gc = num_sms() * 8;  // chunk kernels (a warp per chunk): persistent over the level's chunks
     int level = 0;
     for (;; ++level) {
         int32_t h_S = 0;
@@ -876,13 +852,16 @@ extern "C" int hacc_rcb_build(const hacc_mesh *mesh, const float *x, const float
         int rc = scan_exclusive_i32(B.nchunk, B.chunk_base, B.Smax, B.scan_ws, st);
         if (rc) return rc;
         HACC_CUDA_TRY(cudaMemsetAsync(B.chunk_left, 0, (size_t)B.Cmax * sizeof(int32_t), st));
-        k_rcb_reduce<<<gc, CT, 0, st>>>(grp, S_in, B.chunk_base, B.Smax, qa, B.stat);
+        k_rcb_chunk_map<<<grid_for(B.Cmax, 16), 256, 0, st>>>(S_in, B.chunk_base, B.Smax, B.chunk_group);
         HACC_LAUNCH_CHECK();
-        k_rcb_count<<<gc, CT, 0, st>>>(grp, S_in, B.chunk_base, B.Smax, qa, B.stat, B.chunk_left);
+        k_rcb_reduce<<<gc, 256, 0, st>>>(grp, B.chunk_base, B.chunk_group, B.Smax, qa, B.stat);
+        HACC_LAUNCH_CHECK();
+        k_rcb_count<<<gc, 256, 0, st>>>(grp, B.chunk_base, B.chunk_group, B.Smax, qa, B.stat, B.chunk_left);
         HACC_LAUNCH_CHECK();
         rc = scan_exclusive_i32(B.chunk_left, B.chunk_loff, B.Cmax, B.scan_ws, st);
         if (rc) return rc;
-        k_rcb_scatter<<<gc, CT, 0, st>>>(grp, S_in, B.chunk_base, B.chunk_loff, B.Smax, qa, B.stat, lm, md, qb, B.fin);
+        k_rcb_scatter<<<gc, 256, 0, st>>>(grp, B.chunk_base, B.chunk_group, B.chunk_loff, B.Smax, qa, B.stat, lm,
+                                          md, qb, B.fin);
         HACC_LAUNCH_CHECK();
         k_rcb_next<<<gs, 256, 0, st>>>(grp, S_in, B.chunk_base, B.chunk_loff, B.Smax, B.stat, lm, md, cap,
                                        tree->node_qbox, B.kids, status);

@@ -56,6 +56,7 @@ extern "C" {
 #define HACC_STATUS_CAPACITY 1u /* task buffer too small: some tasks were dropped */
 #define HACC_STATUS_TIMEOUT 2u  /* a bounded device wait gave up; results invalid */
 #define HACC_STATUS_NONFINITE 4u /* a position was NaN or infinite (binned to 0) */
+#define HACC_STATUS_SKIN 8u      /* a drifted offset left its cell widened by skin/2: re-bin */
 
 /* One periodic volume of the chaining mesh (64 bytes).  Filled on the host by
  * hacc_mesh_plan, then copied by the caller to device memory. */
@@ -374,6 +375,20 @@ int hacc_count_pairs(const hacc_mesh *mesh, const hacc_binned *binned, const hac
 int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy, float *vz, const float *ax,
               const float *ay, const float *az, float dt_kick, float *x, float *y, float *z,
               float dt_drift, void *stream);
+
+/* Stream map on the binned particles, for re-binning amortisation over
+ * short-range sub-cycles (Eq. 6): every sorted record's cell-relative offset
+ * moves by dt v of its particle (o <- fma(dt, v, o) in float32; v [N] in input
+ * order, looked up through perm), so the pair calls can run again without
+ * re-binning.  The lists stay complete while every particle stays within
+ * skin/2 of its cell box, i.e. if they were built for r_c + skin (plan the
+ * mesh with rcut = r_c + skin and cell_min >= r_c + skin): an offset outside
+ * [-skin/2, w + skin/2) on any axis sets HACC_STATUS_SKIN, after which the
+ * caller must re-bin.  The input-order positions are not touched (drift them
+ * with hacc_kick and no accelerations).  Not in the paper, whose sub-cycles
+ * rebuild the tree walk each time. */
+int hacc_drift_offsets(const hacc_mesh *mesh, const hacc_binned *binned, const float *vx, const float *vy,
+                       const float *vz, float dt, float skin, uint32_t *status, void *stream);
 
 /* Bytes of scratch that hacc_moments needs. */
 size_t hacc_moments_workspace_size(int64_t N);

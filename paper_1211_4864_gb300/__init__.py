@@ -10,7 +10,7 @@ fallback: without the CUDA library every call raises.
 
 from ._lib import HaccError, library_path, load  # noqa: F401
 from .sr import (Launch, ShortRange, SRParams, hacc_bin, hacc_bin_noalloc, hacc_build_lists, hacc_count_pairs,  # noqa: F401
-                 hacc_get_status, hacc_kick,
+                 hacc_drift_offsets, hacc_get_status, hacc_kick,
                  hacc_kernel_launches, hacc_mesh_plan, hacc_moments, hacc_rcb_build, hacc_rcb_lists,
                  hacc_sr_force, hacc_sr_force_adjoint, hacc_sr_force_adjoint_symmetric, hacc_sr_force_symmetric,
                  hacc_sr_potential, hacc_version,

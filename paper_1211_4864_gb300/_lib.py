@@ -20,6 +20,7 @@ HACC_ERR_TIMEOUT = -4
 HACC_STATUS_CAPACITY = 1
 HACC_STATUS_TIMEOUT = 2
 HACC_STATUS_NONFINITE = 4
+HACC_STATUS_SKIN = 8
 
 _ERRNAMES = {HACC_ERR_INVALID: "invalid argument", HACC_ERR_CAPACITY: "buffer or workspace too small",
              HACC_ERR_CUDA: "CUDA error", HACC_ERR_TIMEOUT: "timeout"}
@@ -110,6 +111,8 @@ SIGNATURES = {
                                         _P, _P]),
     "hacc_kick": (ctypes.c_int, [_PS(hacc_mesh), ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_float,
                                  _P, _P, _P, ctypes.c_float, _P]),
+    "hacc_drift_offsets": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _P, _P, _P, ctypes.c_float,
+                                          ctypes.c_float, _P, _P]),
     "hacc_moments_workspace_size": (ctypes.c_size_t, [ctypes.c_int64]),
     "hacc_moments": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "hacc_sr_potential": (ctypes.c_int, [_PS(hacc_mesh), _PS(hacc_binned), _PS(hacc_lists), _PS(hacc_sr_params),

@@ -107,10 +107,50 @@ __global__ void __launch_bounds__(MOM_THREADS) k_moments_final(const double *__r
     }
 }
 
+// Stream map on sorted records: o += dt v (one float32 fma per axis); flags a
+// record that leaves its cell widened by skin/2.
+__global__ void __launch_bounds__(256)
+k_drift_offsets(int64_t N, const hacc_volume *__restrict__ vols, int V, const int32_t *__restrict__ perm,
+                const float *__restrict__ vx, const float *__restrict__ vy, const float *__restrict__ vz, float dt,
+                float half_skin, float4 *__restrict__ sorted4, uint32_t *status)
+{
+    bool out = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = perm[k];
+        const float w = vols[find_volume_by_particle(vols, V, k)].w;
+        float4 r = sorted4[k];
+        r.x = fmaf(dt, vx[i], r.x);
+        r.y = fmaf(dt, vy[i], r.y);
+        r.z = fmaf(dt, vz[i], r.z);
+        sorted4[k] = r;
+        const float lo = -half_skin, hi = w + half_skin;
+        out |= !(r.x >= lo && r.x < hi && r.y >= lo && r.y < hi && r.z >= lo && r.z < hi);
+    }
+    if (__any_sync(0xffffffffu, out) && (threadIdx.x & 31) == 0) atomicOr(status, HACC_STATUS_SKIN);
+}
+
 }  // namespace
 }  // namespace hacc
 
 using namespace hacc;
+
+extern "C" int hacc_drift_offsets(const hacc_mesh *mesh, const hacc_binned *binned, const float *vx, const float *vy,
+                                  const float *vz, float dt, float skin, uint32_t *status, void *stream)
+{
+    if (!mesh || !mesh->vols || mesh->V < 1 || !binned || !status || !(skin >= 0.0f)) return HACC_ERR_INVALID;
+    const int64_t N = mesh->N;
+    if (N == 0) return HACC_OK;
+    if (!vx || !vy || !vz || !binned->perm || !binned->sorted4 || !aligned16(binned->sorted4))
+        return HACC_ERR_INVALID;
+    if (binned->cell_origin) return HACC_ERR_INVALID;  // chaining-mesh cells (widths from the volumes)
+    int64_t g = (N + 255) / 256;
+    if (g > (int64_t)num_sms() * 16) g = (int64_t)num_sms() * 16;
+    k_drift_offsets<<<(int)g, 256, 0, as_stream(stream)>>>(N, mesh->vols, mesh->V, binned->perm, vx, vy, vz, dt,
+                                                           0.5f * skin, reinterpret_cast<float4 *>(binned->sorted4),
+                                                           status);
+    HACC_LAUNCH_CHECK();
+    return HACC_OK;
+}
 
 extern "C" int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy, float *vz, const float *ax,
                          const float *ay, const float *az, float dt_kick, float *x, float *y, float *z,

@@ -133,6 +133,11 @@ def hacc_rcb_lists(mesh, tree, lists, entry_cap: int, n_entries, ws, status):
           "hacc_rcb_lists")
 
 
+def hacc_drift_offsets(mesh, binned, vx, vy, vz, dt: float, skin: float, status):
+    check(_lib.load().hacc_drift_offsets(ctypes.byref(mesh), ctypes.byref(binned), _ptr(vx), _ptr(vy), _ptr(vz),
+                                         float(dt), float(skin), _ptr(status), _stream()), "hacc_drift_offsets")
+
+
 def hacc_sr_force(mesh, binned, lists, params: SRParams, ax, ay, az, ws, status, launch: Launch | None = None):
     p = params.c_struct()
     lc = launch.c_struct() if launch is not None else None
@@ -211,17 +216,22 @@ class ShortRange:
 
     def __init__(self, L, vol_off, rcut: float, cell_min: float | None = None, split_T: int = 32,
                  device: str | torch.device = "cuda", builder: str = "mesh", leaf_max: int = 64,
-                 max_depth: int = 48):
+                 max_depth: int = 48, skin: float = 0.0):
         """builder: "mesh" (chaining mesh, hacc_bin + hacc_build_lists) or "rcb"
         (the paper's RCB fat-leaf tree, hacc_rcb_build + hacc_rcb_lists, leaves
-        of at most leaf_max particles; its build synchronises the stream)."""
+        of at most leaf_max particles; its build synchronises the stream).
+        skin (mesh only): lists built for rcut + skin, so that binned particles
+        may drift up to skin/2 (drift_offsets) before the next binning."""
         if builder not in ("mesh", "rcb"):
             raise HaccError(f"unknown list builder {builder!r}")
+        if skin < 0 or (skin > 0 and builder != "mesh"):
+            raise HaccError("a skin needs the chaining mesh and must be non-negative")
         self.builder = builder
+        self.skin = float(skin)
         self.device = torch.device(device)
         self.rcut = float(rcut)
-        self.cell_min = float(cell_min if cell_min is not None else rcut)
-        self.table, self.mesh = hacc_mesh_plan(L, vol_off, self.cell_min, self.rcut)
+        self.cell_min = float(cell_min if cell_min is not None else rcut + skin)
+        self.table, self.mesh = hacc_mesh_plan(L, vol_off, self.cell_min, self.rcut + self.skin)
         self.V = int(self.mesh.V)
         self.N = int(self.mesh.N)
         self.n_cells = int(self.mesh.n_cells)
@@ -366,6 +376,12 @@ class ShortRange:
             hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], a[0], a[1], a[2], dt_kick, pos[0],
                       pos[1], pos[2], dt_drift)
 
+    def drift_offsets(self, v, dt):
+        """The stream map on the binned records (offsets += dt v) so that the
+        pair calls can run again without re-binning; a particle that leaves its
+        cell by more than skin/2 sets HACC_STATUS_SKIN."""
+        hacc_drift_offsets(self.mesh, self.binned, v[0], v[1], v[2], dt, self.skin, self.status)
+
     def stream(self, v, pos, dt, wrap=True):
         """The stream map alone: pos += dt v (float64, wrapped if wrap); v unchanged."""
         hacc_kick(self.mesh if wrap else None, self.N, v[0], v[1], v[2], None, None, None, 0.0, pos[0], pos[1],
@@ -390,18 +406,27 @@ class ShortRange:
         return out
 
     def sks_subcycles(self, pos, v, m, params: SRParams, h: float, n_c: int, a=None,
-                      launch: Launch | None = None):
+                      launch: Launch | None = None, rebin_every: int = 1):
         """n_c short-range sub-cycles S(h/2) K(h) S(h/2) of the split-operator
         step (Eq. 6), in place on pos [3, N] (wrapped into the boxes) and
-        v [3, N]: stream h/2, re-bin, force, kick h, stream h/2.  Every call
-        is a library kernel, so the sequence can be captured in a CUDA graph."""
+        v [3, N]: stream h/2, re-bin, force, kick h, stream h/2.  With
+        rebin_every = k > 1 (and a skin) only every k-th sub-cycle re-bins; in
+        between, the binned offsets are streamed with the positions
+        (drift_offsets) and the lists are reused.  Every call is a library
+        kernel, so the sequence can be captured in a CUDA graph."""
         if a is None:
             a = torch.empty_like(v)
-        for _ in range(n_c):
+        k = max(1, int(rebin_every))
+        for c in range(n_c):
             self.stream(v, pos, 0.5 * h)
-            self.prepare(pos, m)
+            if c % k == 0:
+                self.prepare(pos, m)
+            else:
+                self.drift_offsets(v, 0.5 * h)
             self.force(params, a, launch=launch)
             self.kick(v, a, h, pos, 0.5 * h)
+            if (c + 1) % k != 0 and c + 1 < n_c:  # the next force reuses these records
+                self.drift_offsets(v, 0.5 * h)
         return a
 
     def prepare(self, pos, m, disp=None):

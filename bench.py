@@ -32,26 +32,29 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
+FLOPS_PER_PAIR_EQ = 28  # equal-mass path: no x m_j
 # DRAM bytes of one force launch on clustered256, from ncu (profiles/force_clustered256_dram.md),
 # valid only for the kernel source it was measured on
 # flops per evaluated unordered pair of the symmetric kernel: d 3, s 5, s + eps 1, t^3 2, Horner 10,
 # subtract 1, x m_j and x m_i 2, both accumulations 12
 FLOPS_PER_SYM_PAIR = 36
+FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
 # ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
 # they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2242479872 + 969879296,
+    "gather": {"workload": "clustered256", "bytes": 2221974272 + 966593024,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "d744c9399634f0772f610da413d65a764cab4258a87199d33e269e4aa327c753"},
-    "symmetric": {"workload": "clustered256", "bytes": 2829236736 + 1512726272,
+               "sha256": "4907fe99d6391d9aaa1359748f060e716cd402fd7c1ea9e0a3aa8a98fa423662"},
+    "symmetric": {"workload": "clustered256", "bytes": 2817565440 + 1504486144,
                   "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
-                  "sha256": "092ff2768bbc88e8b87096c70dc1ed8eebcf9dced40d91cb30667a53e57fe8d5"},
+                  "sha256": "adad5997e885e37902084014fac552b49c023a0767fc82c3a70a380775e26c94"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
 WORKLOADS = {
     "clustered256": "256^3 = 16,777,216 particles, L = 256, 60% uniform + 40% in 2000 NFW halos "
-                    "(log-uniform masses, c = 5-10, seed 3), r_c = 3, eps = 0.01, cell_min = 3, one force "
+                    "(log-uniform halo sizes, c = 5-10, seed 3), unit particle masses, r_c = 3, eps = 0.01, "
+                    "cell_min = 3, one force "
                     "evaluation + kick per step",
     "lattice128": "128^3 = 2,097,152 particles, L = 128, unit lattice + Gaussian displacement rms 0.5 "
                   "(seed 2), r_c = 3, eps = 0.01, cell_min = 3, one force evaluation + kick per step",
@@ -286,6 +289,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         launches = (hs.hacc_kernel_launches() - l0)
     t_force = statistics.mean(f0[k].elapsed_time(f1[k]) for k in range(args.steps))
+    eq = sr.equal_mass  # untimed: which force path ran (all masses equal -> the equal-mass path)
+    fpp_g = FLOPS_PER_PAIR_EQ if eq else FLOPS_PER_PAIR
+    fpp_s = FLOPS_PER_SYM_PAIR_EQ if eq else FLOPS_PER_SYM_PAIR
     total_pairs = ranks.sum(float(pairs)) * args.steps
     value = total_pairs / (t_ms_max * 1e-3)
     within = sr.pairs_within_cutoff(prm)  # untimed: the pairs that actually interact
@@ -317,13 +323,14 @@ def run_ours(args):
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * 128 * 2 * f_max * 1e6 / 1e12
     if args.kernel == "symmetric":
-        # executed work: each unordered candidate pair once, FLOPS_PER_SYM_PAIR flops
-        achieved = FLOPS_PER_SYM_PAIR * (pairs / 2) / (t_force * 1e-3) / 1e12
-        kname, fpp = "k_pairs_sym (hacc_sr_force_symmetric)", {"flops_per_unordered_pair": FLOPS_PER_SYM_PAIR,
+        # executed work: each unordered candidate pair once, fpp_s flops
+        achieved = fpp_s * (pairs / 2) / (t_force * 1e-3) / 1e12
+        kname, fpp = "k_pairs_sym (hacc_sr_force_symmetric)", {"flops_per_unordered_pair": fpp_s,
                                                                "unordered_pairs": pairs // 2}
     else:
-        achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
-        kname, fpp = "k_pairs<FORCE> (hacc_sr_force)", {"flops_per_pair": FLOPS_PER_PAIR}
+        achieved = fpp_g * pairs / (t_force * 1e-3) / 1e12
+        kname, fpp = "k_pairs<FORCE> (hacc_sr_force)", {"flops_per_pair": fpp_g}
+    fpp["mass_path"] = "equal (every particle mass equal)" if eq else "general (per-particle masses)"
     out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved,
                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                        "traffic": force_traffic(args.config, args.kernel),
@@ -340,7 +347,8 @@ def run_ours(args):
 
     # the other pair kernel on the same lists: Newton-III symmetric vs gather
     if ranks.rank == 0:
-        out["newton3"] = newton3(torch, sr, prm, launch, launch_sym, a, pairs, args.kernel, t_force, peak)
+        out["newton3"] = newton3(torch, sr, prm, launch, launch_sym, a, pairs, args.kernel, t_force, peak,
+                                 fpp_g, fpp_s)
 
     # forward + adjoint on the same lists (not part of the timed step)
     lam = torch.randn((3, w.N), device=dev, generator=torch.Generator(device=dev).manual_seed(7))
@@ -371,6 +379,20 @@ def run_ours(args):
                           "symmetric": {"force_ms": t_symf, "adjoint_ms": t_adj_sym,
                                         "ratio_fwd_plus_adj_over_fwd": (t_symf + t_adj_sym) / t_symf,
                                         "adjoint_speedup_vs_gather": t_adj / t_adj_sym}}
+    out["fwd_adjoint"]["mass_path"] = "equal" if eq else "general"
+    if eq and ranks.rank == 0 and "newton3" in out:
+        # the general path (flag withheld) of all four pair kernels on the same particles and lists
+        mp = mass_paths(torch, sr, pos, m, prm, lam, (launch, launch_sym, launch_adj, launch_adj_sym), a, pairs,
+                        peak, {"gather_force_ms": t_gather, "symmetric_force_ms": t_symf, "adjoint_ms": t_adj,
+                               "adjoint_symmetric_ms": t_adj_sym})
+        out["mass_paths"] = mp
+        gen = mp["general"]
+        out["fwd_adjoint"]["general_mass_path"] = {
+            "force_ms": gen["gather_force_ms"], "adjoint_ms": gen["adjoint_ms"],
+            "ratio_fwd_plus_adj_over_fwd": (gen["gather_force_ms"] + gen["adjoint_ms"]) / gen["gather_force_ms"],
+            "symmetric": {"force_ms": gen["symmetric_force_ms"], "adjoint_ms": gen["adjoint_symmetric_ms"],
+                          "ratio_fwd_plus_adj_over_fwd": (gen["symmetric_force_ms"] + gen["adjoint_symmetric_ms"])
+                          / gen["symmetric_force_ms"]}}
 
     # differentiation workload: forward trajectory vs forward + backward
     if not args.no_diff and ranks.rank == 0:
@@ -503,7 +525,7 @@ def binning_rate(torch, sr, pos, m, w, peaks, reps=5):
                     "gather of the records; the sort's intermediate passes are not counted as algorithmic bytes"}
 
 
-def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, reps=3):
+def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, fpp_g, fpp_s, reps=3):
     """Gather kernel (every particle sums its own list: each pair evaluated
     twice) against the Newton-III symmetric kernel (each pair once, applied to
     both), same lists, same inputs; the one the step did not use is timed
@@ -525,11 +547,50 @@ def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak,
     rel = float((a.double() - b.double()).norm() / b.double().norm())
     return {"gather_force_ms": t_g, "symmetric_force_ms": t_s, "speedup": t_g / t_s,
             "interactions_per_s": {"gather": pairs / (t_g * 1e-3), "symmetric": pairs / (t_s * 1e-3)},
-            "fp32_frac_executed": {"gather": FLOPS_PER_PAIR * pairs / (t_g * 1e-3) / 1e12 / peak,
-                                   "symmetric": FLOPS_PER_SYM_PAIR * pairs / 2 / (t_s * 1e-3) / 1e12 / peak},
+            "fp32_frac_executed": {"gather": fpp_g * pairs / (t_g * 1e-3) / 1e12 / peak,
+                                   "symmetric": fpp_s * pairs / 2 / (t_s * 1e-3) / 1e12 / peak},
             "force_rel_diff": rel,
             "launch": {"gather": launch.__dict__ if launch else "default",
                        "symmetric": launch_sym.__dict__ if launch_sym else "default"}}
+
+
+def mass_paths(torch, sr, pos, m, prm, lam, launches, a, pairs, peak, eq_ms, reps=3):
+    """The four pair kernels (gather and symmetric force, gather and symmetric
+    adjoint without dL/dm) on the same particles and lists with the equal-mass
+    flag withheld, i.e. the general path with per-particle masses in every
+    pair, against the equal-mass path the rest of the line ran; the forces of
+    the two paths are compared."""
+    launch, launch_sym, launch_adj, launch_adj_sym = launches
+    sr.set_equal_mass_path(False)
+    sr.prepare(pos, m)
+    b = torch.empty_like(a)
+    runs = (("gather_force_ms", lambda: sr.force(prm, b, launch=launch)),
+            ("symmetric_force_ms", lambda: sr.force_symmetric(prm, b, launch=launch_sym)),
+            ("adjoint_ms", lambda: sr.adjoint(prm, lam, want_gm=False, launch=launch_adj)),
+            ("adjoint_symmetric_ms", lambda: sr.adjoint_symmetric(prm, lam, want_gm=False, launch=launch_adj_sym)))
+    t = {}
+    for name, fn in runs:
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t[name] = e0.elapsed_time(e1) / reps
+        if name == "symmetric_force_ms":
+            rel = float((a.double() - b.double()).norm() / b.double().norm())  # a: the step's force
+    sr.check_status()
+    sr.set_equal_mass_path(True)
+    sr.prepare(pos, m)
+    torch.cuda.synchronize()
+    t["fp32_frac_executed"] = {
+        "gather": FLOPS_PER_PAIR * pairs / (t["gather_force_ms"] * 1e-3) / 1e12 / peak,
+        "symmetric": FLOPS_PER_SYM_PAIR * pairs / 2 / (t["symmetric_force_ms"] * 1e-3) / 1e12 / peak}
+    return {"general": t,
+            "equal_mass_speedup": {k: t[k] / eq_ms[k] for k in eq_ms},
+            "force_rel_diff_equal_vs_general": rel}
 
 
 def tree_vs_mesh(torch, hs, sr, pos, m, w, prm, launch, launch_sym, split_T, t_force, t_sym, pairs, within,

@@ -95,6 +95,16 @@ typedef struct hacc_binned {
     float *sorted4;      /* [4 N] per sorted slot (ox, oy, oz, m), o = cell-relative offset */
     float *cell_origin;  /* [4 n_cells] (x, y, z, 0) origin the offsets of each cell are taken from,
                             or NULL for the chaining mesh (cell (cx, cy, cz) sits at float32 c w) */
+    uint32_t *mass_varies; /* device word or NULL.  hacc_bin, hacc_bin_noalloc and hacc_rcb_build set
+                            it to 0 when every mass is bitwise equal to the first particle's (N = 0
+                            included) and to 1 otherwise.  When it reads 0, the force calls
+                            (hacc_sr_force, hacc_sr_force_symmetric) and the adjoint calls take
+                            their equal-mass path: the pair sums hold f d (adjoint: V = sum f,
+                            X = sum 2 f' (d.(lam_j - lam_i)) d) and each particle's total is
+                            scaled once by its own mass, the common m (sum_j m_j f d =
+                            m sum_j f d), which saves per-pair mass products; the results agree
+                            with the general path to float32 rounding.  NULL: the general path,
+                            always. */
 } hacc_binned;
 
 /* Output of hacc_build_lists. */
@@ -170,7 +180,8 @@ size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
  * trajectory kept as a fixed reference plus a small drift displacement so
  * keeps its float64 position to float32 precision of a cell-relative offset.
  * Within a cell the sorted order is ascending input index (bit-exact and
- * deterministic).  x, y, z, m: [N] input order.  Writes every array of `out`.
+ * deterministic).  x, y, z, m: [N] input order.  Writes every array of `out`
+ * (out->mass_varies if not NULL).
  * A non-finite coordinate sets HACC_STATUS_NONFINITE and is binned as 0. */
 int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
              const float *dx, const float *dy, const float *dz, const float *m,
@@ -257,8 +268,8 @@ size_t hacc_rcb_build_workspace_size(const hacc_mesh *mesh, int32_t leaf_max);
  * q <= split, the partition is stable; a group whose box is a point is
  * halved by position (cnt/2 left).  Leaves are numbered depth first, left
  * first (= by first slot).  Writes every array of `tree`, and of `out`:
- * perm, sorted4 with o = fl32(xw - origin) (float64 difference), cell_of if
- * not NULL; `out->cell_start` and `out->cell_origin` are not touched (point
+ * perm, sorted4 with o = fl32(xw - origin) (float64 difference), cell_of and
+ * mass_varies if not NULL; `out->cell_start` and `out->cell_origin` are not touched (point
  * them at tree->leaf_start and tree->leaf_origin for the pair calls).
  * Level-synchronous on the GPU: it SYNCHRONISES `stream` once per tree level
  * to read the number of groups left, so it cannot be captured in a CUDA

@@ -44,7 +44,7 @@ class hacc_mesh(ctypes.Structure):
 
 class hacc_binned(ctypes.Structure):
     _fields_ = [("cell_of", ctypes.c_void_p), ("cell_start", ctypes.c_void_p), ("perm", ctypes.c_void_p),
-                ("sorted4", ctypes.c_void_p), ("cell_origin", ctypes.c_void_p)]
+                ("sorted4", ctypes.c_void_p), ("cell_origin", ctypes.c_void_p), ("mass_varies", ctypes.c_void_p)]
 
 
 class hacc_lists(ctypes.Structure):

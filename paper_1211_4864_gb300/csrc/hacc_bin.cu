@@ -68,14 +68,16 @@ __device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, con
 }
 
 // Pass 1: per particle, its cell key, its (offset, mass) record in input
-// order, and the cell histogram.
+// order, and the cell histogram; with mass_varies, whether any mass differs
+// from the first particle's (N > 0).
 __global__ void __launch_bounds__(KEY_THREADS)
 k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *__restrict__ x,
            const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dx,
            const float *__restrict__ dy, const float *__restrict__ dz, const float *__restrict__ m,
            int32_t *__restrict__ cell_of, int32_t *__restrict__ keys, float4 *__restrict__ rec,
-           int32_t *__restrict__ counts, uint32_t *status)
+           int32_t *__restrict__ counts, uint32_t *status, uint32_t *mass_varies)
 {
+    MassCheck mc(m, mass_varies);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         int v = find_volume_by_particle(vols, V, i);
@@ -90,11 +92,13 @@ k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *
         keys[i] = key;
         r.w = m[i];
         rec[i] = r;
+        mc.check(r.w);
         // one atomic per distinct cell of the warp: consecutive particles of a halo share cells
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, key);
         if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
     }
+    mc.finish();
 }
 
 // Radix pass, step 1: digit histogram of each 4096-key tile, digit-major.
@@ -290,9 +294,11 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     cudaStream_t st = as_stream(stream);
 
     HACC_CUDA_TRY(cudaMemsetAsync(b.counts, 0, (size_t)mesh->n_cells * 4, st));
+    if (out->mass_varies) HACC_CUDA_TRY(cudaMemsetAsync(out->mass_varies, 0, sizeof(uint32_t), st));
     if (N > 0) {
         k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(
-            mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m, out->cell_of, b.keys, b.rec, b.counts, status);
+            mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m, out->cell_of, b.keys, b.rec, b.counts, status,
+            out->mass_varies);
         HACC_LAUNCH_CHECK();
     }
     int rc = scan_exclusive_i32(b.counts, out->cell_start, mesh->n_cells, b.scan_ws, st);

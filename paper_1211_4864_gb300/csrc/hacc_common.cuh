@@ -75,6 +75,28 @@ __device__ __forceinline__ int find_volume_by_cell(const hacc_volume *vols, int 
     return lo;
 }
 
+// Equal-mass detection (hacc_binned::mass_varies): every thread compares the
+// masses it writes bitwise with m[0], and one barrier-OR at the end of the
+// kernel lets thread 0 of a block that saw a difference set *flag.  Built at
+// the top of a kernel whose threads all run to the end (finish() is a block
+// barrier when flag is set); m[0] is read only with a flag (then N > 0); the
+// host clears *flag beforehand.
+struct MassCheck {
+    uint32_t *flag;
+    uint32_t m0;
+    bool differs;
+    __device__ __forceinline__ MassCheck(const float *m, uint32_t *f) : flag(f), m0(0u), differs(false)
+    {
+        if (f) m0 = __float_as_uint(m[0]);
+    }
+    __device__ __forceinline__ void check(float mi) { differs |= __float_as_uint(mi) != m0; }
+    __device__ __forceinline__ void finish()
+    {
+        if (!flag) return;  // a kernel argument: every thread of the grid takes the same branch
+        if (__syncthreads_or(differs) && threadIdx.x == 0) atomicOr(flag, 1u);
+    }
+};
+
 // Two cells whose integer offsets are (dx, dy, dz) can hold a pair closer
 // than rc iff the minimum distance of the boxes is below rc (float64).
 __host__ __device__ __forceinline__ bool cells_within(int dx, int dy, int dz, double w, double rc)
@@ -97,7 +119,7 @@ __host__ __device__ __forceinline__ bool cells_within(int dx, int dy, int dz, do
 size_t scan_workspace_bytes(int64_t n);
 int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, cudaStream_t st);
 
-// Stable sort of indices by int32 key (LSD radix, 8-bit digits, only the low
+// Stable sort of indices by int32 key (LSD radix, 10-bit digits, only the low
 // `bits` bits significant): order[k] = index of the k-th smallest key, ties
 // in index order.  ws: sort_workspace_bytes(N).  Deterministic.
 size_t sort_workspace_bytes(int64_t N);

@@ -58,9 +58,11 @@ struct Acc<FORCE, IPL> : AccN<IPL, 3> {};
 template <int IPL>
 struct Acc<POTENTIAL, IPL> : AccN<IPL, 1> {};
 
-// One pair of the forward law, accumulated into acc[3].  The cutoff test is
-// a compare whose predicate guards the three accumulating fma (no branch, no
-// select): the paper folds the same test into the loop with fsel (Sec. III).
+// One pair of the forward law, accumulated into acc[3] (EQ, equal masses:
+// f d, the mass applied to the total).  The cutoff test is a compare whose
+// predicate guards the three accumulating fma (no branch, no select): the
+// paper folds the same test into the loop with fsel (Sec. III).
+template <bool EQ>
 __device__ __forceinline__ void pair_force(const float4 p, float oxp, float oyp, float ozp, const PairConsts &K,
                                            float *acc)
 {
@@ -70,7 +72,7 @@ __device__ __forceinline__ void pair_force(const float4 p, float oxp, float oyp,
     float t2 = t * t;
     float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
                    K.nc[0]);
-    float g = fmaf(t2, t, q) * p.w;
+    float g = EQ ? fmaf(t2, t, q) : fmaf(t2, t, q) * p.w;
     asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %3, %4;\n\t"
         "@p fma.rn.f32 %0, %5, %6, %0;\n\t@p fma.rn.f32 %1, %5, %7, %1;\n\t@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
         : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2])
@@ -79,7 +81,7 @@ __device__ __forceinline__ void pair_force(const float4 p, float oxp, float oyp,
 
 // Forward pair loop over one staged tile: every staged j meets the IPL i
 // particles of this lane.  Unrolled by hand, four j per trip.
-template <int IPL>
+template <int IPL, bool EQ>
 __device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n, const float (&op)[IPL][3],
                                            const PairConsts &K, Acc<FORCE, IPL> &A)
 {
@@ -88,16 +90,16 @@ __device__ __forceinline__ void tile_force(const float4 *__restrict__ tj, int n,
         const float4 p0 = tj[j], p1 = tj[j + 1], p2 = tj[j + 2], p3 = tj[j + 3];
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
-            pair_force(p0, op[u][0], op[u][1], op[u][2], K, A.a[u]);
-            pair_force(p1, op[u][0], op[u][1], op[u][2], K, A.a[u]);
-            pair_force(p2, op[u][0], op[u][1], op[u][2], K, A.a[u]);
-            pair_force(p3, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force<EQ>(p0, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force<EQ>(p1, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force<EQ>(p2, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+            pair_force<EQ>(p3, op[u][0], op[u][1], op[u][2], K, A.a[u]);
         }
     }
     for (; j < n; ++j) {
         const float4 p = tj[j];
 #pragma unroll
-        for (int u = 0; u < IPL; ++u) pair_force(p, op[u][0], op[u][1], op[u][2], K, A.a[u]);
+        for (int u = 0; u < IPL; ++u) pair_force<EQ>(p, op[u][0], op[u][1], op[u][2], K, A.a[u]);
     }
 }
 
@@ -148,8 +150,10 @@ __device__ __forceinline__ void tile_potential(const float4 *__restrict__ tj, in
 // fp2 = 2 f_SR'(s):  U += f lam_j ;  V += m_j f ;
 // X += fp2 (m_i (d.lam_j) - m_j (d.lam_i)) d ;  G += f (d.lam_j).
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
+// Equal masses (EQ): V += f and X += fp2 (d.(lam_j - lam_i)) d, so that
+// dL/dx_i = m (U - lam_i V + X); one dot product instead of two without G.
 // One pair of the adjoint, accumulated into acc[8] = (U, V, X, G) of one i.
-template <bool GM>
+template <bool GM, bool EQ>
 __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, float oxp, float oyp, float ozp,
                                              float mi, float lix, float liy, float liz, const PairConsts &K,
                                              float (&acc)[ADJ_NACC])
@@ -165,8 +169,16 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
     float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
     float fp2 = fmaf(-3.0f, t3 * t2, qp);
     float dlj = fmaf(dz, l.z, fmaf(dy, l.y, dx * l.x));
-    float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
-    float r = fp2 * fmaf(mi, dlj, -(p.w * dli));
+    float r;
+    if constexpr (EQ && !GM) {
+        r = fp2 * fmaf(dz, l.z - liz, fmaf(dy, l.y - liy, dx * (l.x - lix)));
+    } else if constexpr (EQ) {
+        r = fp2 * (dlj - fmaf(dz, liz, fmaf(dy, liy, dx * lix)));
+    } else {
+        const float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
+        r = fp2 * fmaf(mi, dlj, -(p.w * dli));
+    }
+    const float mj = EQ ? 1.0f : p.w;
     // the accumulations of this pair happen only inside the cutoff
     if constexpr (GM) {
         asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
@@ -176,7 +188,7 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
             "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
             : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]),
               "+f"(acc[7])
-            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
+            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(mj), "f"(r), "f"(dx), "f"(dy),
               "f"(dz), "f"(dlj));
     } else {
         asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %7, %8;\n\t"
@@ -184,13 +196,13 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
             "@p fma.rn.f32 %3, %13, %9, %3;\n\t"
             "@p fma.rn.f32 %4, %14, %15, %4;\n\t@p fma.rn.f32 %5, %14, %16, %5;\n\t@p fma.rn.f32 %6, %14, %17, %6;\n\t}"
             : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6])
-            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(p.w), "f"(r), "f"(dx), "f"(dy),
+            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(mj), "f"(r), "f"(dx), "f"(dy),
               "f"(dz));
     }
 }
 
 // Adjoint pair loop over one staged tile (positions tj, cotangents tl).
-template <int MODE, int IPL>
+template <int MODE, int IPL, bool EQ>
 __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, const float4 *__restrict__ tl, int n,
                                              const float (&op)[IPL][3], const float4 (&oi)[IPL],
                                              const float4 (&li)[IPL], const PairConsts &K, AccAdj<MODE, IPL> &A)
@@ -201,15 +213,18 @@ __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, cons
         // one i per lane: two j per trip for independent work
         for (; j + 2 <= n; j += 2) {
             const float4 p0 = tj[j], p1 = tj[j + 1], l0 = tl[j], l1 = tl[j + 1];
-            pair_adjoint<GM>(p0, l0, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K, A.p[0]);
-            pair_adjoint<GM>(p1, l1, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K, A.p[0]);
+            pair_adjoint<GM, EQ>(p0, l0, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K,
+                                 A.p[0]);
+            pair_adjoint<GM, EQ>(p1, l1, op[0][0], op[0][1], op[0][2], oi[0].w, li[0].x, li[0].y, li[0].z, K,
+                                 A.p[0]);
         }
     }
     for (; j < n; ++j) {
         const float4 p0 = tj[j], l0 = tl[j];
 #pragma unroll
         for (int u = 0; u < IPL; ++u)
-            pair_adjoint<GM>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K, A.p[u]);
+            pair_adjoint<GM, EQ>(p0, l0, op[u][0], op[u][1], op[u][2], oi[u].w, li[u].x, li[u].y, li[u].z, K,
+                                 A.p[u]);
     }
 }
 
@@ -226,7 +241,7 @@ __device__ __forceinline__ auto make_acc(float *comp, int lane)
         return AccAdj<MODE, IPL>(comp, lane);
 }
 
-template <int MODE, int JT, int STAGES, int IPL>
+template <int MODE, int JT, int STAGES, int IPL, bool EQ>
 __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> &ring, float *comp, int lane,
                                          int c, int ib, int ie, const hacc_volume &vol)
 {
@@ -314,11 +329,11 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
                     }
                 }
                 if constexpr (MODE == FORCE)
-                    tile_force<IPL>(tj + filled, n, op, K, A);
+                    tile_force<IPL, EQ>(tj + filled, n, op, K, A);
                 else if constexpr (MODE == POTENTIAL)
                     tile_potential<IPL>(tj + filled, n, op, K, A);
                 else
-                    tile_adjoint<MODE, IPL>(tj + filled, tj + JT + filled, n, op, oi, li, K, A);
+                    tile_adjoint<MODE, IPL, EQ>(tj + filled, tj + JT + filled, n, op, oi, li, K, A);
                 filled += n;
                 coff += n;
             }
@@ -332,7 +347,11 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
     for (int u = 0; u < IPL; ++u) {
         if (!active[u]) continue;
         const int o = a.perm[ib + lane + 32 * u];
-        if constexpr (MODE == FORCE) {
+        if constexpr (MODE == FORCE && EQ) {
+            a.out_x[o] = oi[u].w * (A.h[u][0] + A.l[u][0]);
+            a.out_y[o] = oi[u].w * (A.h[u][1] + A.l[u][1]);
+            a.out_z[o] = oi[u].w * (A.h[u][2] + A.l[u][2]);
+        } else if constexpr (MODE == FORCE) {
             a.out_x[o] = A.h[u][0] + A.l[u][0];
             a.out_y[o] = A.h[u][1] + A.l[u][1];
             a.out_z[o] = A.h[u][2] + A.l[u][2];
@@ -341,11 +360,17 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             const float self = pair_potential_of(K.eps, K);
             a.out_x[o] = (A.h[u][0] + A.l[u][0]) - oi[u].w * self;
         } else {
-            // dL/dx_i = m_i U - lam_i V + X ;  dL/dm_i = -G
+            // dL/dx_i = m_i U - lam_i V + X (equal masses: m (U - lam_i V + X)) ;  dL/dm_i = -G
             const float Vs = A.total(u, 3);
-            a.out_x[o] = fmaf(oi[u].w, A.total(u, 0), fmaf(-li[u].x, Vs, A.total(u, 4)));
-            a.out_y[o] = fmaf(oi[u].w, A.total(u, 1), fmaf(-li[u].y, Vs, A.total(u, 5)));
-            a.out_z[o] = fmaf(oi[u].w, A.total(u, 2), fmaf(-li[u].z, Vs, A.total(u, 6)));
+            if constexpr (EQ) {
+                a.out_x[o] = oi[u].w * (A.total(u, 0) + fmaf(-li[u].x, Vs, A.total(u, 4)));
+                a.out_y[o] = oi[u].w * (A.total(u, 1) + fmaf(-li[u].y, Vs, A.total(u, 5)));
+                a.out_z[o] = oi[u].w * (A.total(u, 2) + fmaf(-li[u].z, Vs, A.total(u, 6)));
+            } else {
+                a.out_x[o] = fmaf(oi[u].w, A.total(u, 0), fmaf(-li[u].x, Vs, A.total(u, 4)));
+                a.out_y[o] = fmaf(oi[u].w, A.total(u, 1), fmaf(-li[u].y, Vs, A.total(u, 5)));
+                a.out_z[o] = fmaf(oi[u].w, A.total(u, 2), fmaf(-li[u].z, Vs, A.total(u, 6)));
+            }
             if constexpr (MODE == ADJOINT_GM) a.out_m[o] = -A.total(u, 7);
         }
     }
@@ -360,9 +385,16 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
 // memory, which caps it at 2 CTAs, so it may use up to 128 registers.
 __host__ __device__ constexpr int min_ctas(int mode) { return is_adjoint(mode) ? 2 : 3; }
 
-template <int MODE, int JT, int STAGES>
+// EQ (force and adjoint): the equal-mass instantiation; as for the
+// symmetric kernel both are launched and the one that does not match the
+// flag returns.
+template <int MODE, int JT, int STAGES, bool EQ>
 __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
 {
+    if constexpr (MODE != POTENTIAL) {
+        const bool eq = a.mass_varies && *a.mass_varies == 0u;
+        if (eq != EQ) return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int WARP_BYTES = warp_smem_bytes(MODE, JT, STAGES);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -393,9 +425,9 @@ __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
         for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
             const int se = min(sb + 64, task.z);
             if (se - sb > 32)
-                ok = run_task<MODE, JT, STAGES, 2>(a, ring, comp, lane, task.x, sb, se, vol);
+                ok = run_task<MODE, JT, STAGES, 2, EQ>(a, ring, comp, lane, task.x, sb, se, vol);
             else
-                ok = run_task<MODE, JT, STAGES, 1>(a, ring, comp, lane, task.x, sb, se, vol);
+                ok = run_task<MODE, JT, STAGES, 1, EQ>(a, ring, comp, lane, task.x, sb, se, vol);
         }
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
@@ -461,11 +493,11 @@ k_count_pairs(const KArgs a, unsigned long long *__restrict__ total)
 }
 
 
-template <int MODE, int JT, int STAGES>
-int launch_t(const KArgs &a, int warps, int ctas_per_sm, cudaStream_t st)
+template <int MODE, int JT, int STAGES, bool EQ>
+int launch_one(const KArgs &a, int warps, int ctas_per_sm, cudaStream_t st)
 {
     const size_t smem = (size_t)warps * warp_smem_bytes(MODE, JT, STAGES);
-    auto kern = k_pairs<MODE, JT, STAGES>;
+    auto kern = k_pairs<MODE, JT, STAGES, EQ>;
     if (smem > 48 * 1024)
         HACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -475,6 +507,18 @@ int launch_t(const KArgs &a, int warps, int ctas_per_sm, cudaStream_t st)
     kern<<<num_sms() * per_sm, warps * 32, smem, st>>>(a);
     HACC_LAUNCH_CHECK();
     return HACC_OK;
+}
+
+template <int MODE, int JT, int STAGES>
+int launch_t(const KArgs &a, int warps, int ctas_per_sm, cudaStream_t st)
+{
+    if constexpr (MODE != POTENTIAL) {
+        if (a.mass_varies) {
+            const int rc = launch_one<MODE, JT, STAGES, true>(a, warps, ctas_per_sm, st);
+            if (rc) return rc;
+        }
+    }
+    return launch_one<MODE, JT, STAGES, false>(a, warps, ctas_per_sm, st);
 }
 
 template <int MODE>

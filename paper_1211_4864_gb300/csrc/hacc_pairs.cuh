@@ -47,6 +47,7 @@ struct KArgs {
     int32_t *counter;
     uint32_t *status;
     PairConsts k;
+    const uint32_t *mass_varies;  // 0: every mass equal (the equal-mass force paths); NULL: general
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -355,6 +356,7 @@ KArgs base_args(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lis
     a.origin = reinterpret_cast<const float4 *>(binned->cell_origin);
     a.pos = reinterpret_cast<const float4 *>(binned->sorted4);
     a.perm = binned->perm;
+    a.mass_varies = binned->mass_varies;
     a.status = status;
     pair_consts(p, a.k);
     return a;

@@ -415,8 +415,9 @@ k_rcb_leaf_fill(const hacc_volume *__restrict__ vols, int V, const float *__rest
                 const float *__restrict__ z, const float *__restrict__ m, const int4 *__restrict__ fin,
                 const int32_t *__restrict__ leaf_start, const int32_t *__restrict__ n_leaves,
                 int32_t *__restrict__ leaf_qbox, float4 *__restrict__ leaf_origin, int32_t *__restrict__ perm,
-                float4 *__restrict__ sorted4, int32_t *__restrict__ cell_of)
+                float4 *__restrict__ sorted4, int32_t *__restrict__ cell_of, uint32_t *mass_varies)
 {
+    MassCheck mc(m, mass_varies);
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int nl = *n_leaves;
@@ -447,12 +448,15 @@ k_rcb_leaf_fill(const hacc_volume *__restrict__ vols, int V, const float *__rest
             const float yw = wrap32(finite_or_zero(y[i], bad), L);
             const float zw = wrap32(finite_or_zero(z[i], bad), L);
             perm[k] = i;
+            const float mi = m[i];
             sorted4[k] = make_float4(__double2float_rn(__dsub_rn((double)xw, (double)ox)),
                                      __double2float_rn(__dsub_rn((double)yw, (double)oy)),
-                                     __double2float_rn(__dsub_rn((double)zw, (double)oz)), m[i]);
+                                     __double2float_rn(__dsub_rn((double)zw, (double)oz)), mi);
+            mc.check(mi);
             if (cell_of) cell_of[i] = (int32_t)l;
         }
     }
+    mc.finish();
 }
 
 // Children and roots recorded by first slot become leaf ids.
@@ -827,6 +831,7 @@ extern "C" int hacc_rcb_build(const hacc_mesh *mesh, const float *x, const float
     const int lm = tree->leaf_max, md = tree->max_depth;
     const int64_t cap = tree->leaf_cap;
 
+    if (out->mass_varies) HACC_CUDA_TRY(cudaMemsetAsync(out->mass_varies, 0, sizeof(uint32_t), st));
     if (N > 0) {
         // every final slot is written by exactly one scatter; cleared first so that no
         // index read from it can leave [0, N) whatever happens
@@ -889,7 +894,8 @@ extern "C" int hacc_rcb_build(const hacc_mesh *mesh, const float *x, const float
         k_rcb_leaf_fill<<<grid_for(N, 16), 256, 0, st>>>(mesh->vols, V, x, y, z, m, B.fin, tree->leaf_start,
                                                          tree->n_leaves, tree->leaf_qbox,
                                                          reinterpret_cast<float4 *>(tree->leaf_origin), out->perm,
-                                                         reinterpret_cast<float4 *>(out->sorted4), out->cell_of);
+                                                         reinterpret_cast<float4 *>(out->sorted4), out->cell_of,
+                                                         out->mass_varies);
         HACC_LAUNCH_CHECK();
     }
     k_rcb_fix_children<<<grid_for(2 * (N / 2 + 1) + V, 16), 256, 0, st>>>(B.leaf_of_pos, tree->n_nodes, V,

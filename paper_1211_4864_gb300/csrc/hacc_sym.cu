@@ -21,6 +21,11 @@
 // converts the totals to float32 in input order.  The sums are formed in a
 // run-dependent order, so results agree with the gather kernel to rounding
 // but are not bitwise reproducible.
+//
+// Equal masses (the binning found every mass equal): both sides accumulate
+// f d, the j masses no longer rotate, and each total is scaled by the
+// particle's own mass when it is added (a_i = m sum_j f d, a_j = -m sum_i f d),
+// which takes the two mass products out of every pair.
 #include "hacc_pairs.cuh"
 
 namespace hacc {
@@ -78,20 +83,22 @@ struct JRec {
     int slot;
 };
 
+template <bool EQ>
 __device__ __forceinline__ void rotate_one(JRec &J, int src)
 {
     J.x = __shfl_sync(FULL, J.x, src);
     J.y = __shfl_sync(FULL, J.y, src);
     J.z = __shfl_sync(FULL, J.z, src);
-    J.m = __shfl_sync(FULL, J.m, src);
+    if constexpr (!EQ) J.m = __shfl_sync(FULL, J.m, src);  // equal masses: the lane keeps its own
     J.fx = __shfl_sync(FULL, J.fx, src);
     J.fy = __shfl_sync(FULL, J.fy, src);
     J.fz = __shfl_sync(FULL, J.fz, src);
 }
 
-// One pair, both sides: a_i += m_j f d, f_j -= m_i f d, predicated on the
-// cutoff (and on `ok`, the upper-triangle test of a diagonal block).
-template <bool MASKED>
+// One pair, both sides: a_i += m_j f d, f_j -= m_i f d (equal masses: both
+// += f d), predicated on the cutoff (and on `ok`, the upper-triangle test of a
+// diagonal block).
+template <bool MASKED, bool EQ>
 __device__ __forceinline__ void pair_sym(JRec &J, const float4 &oi, const PairConsts &K, float (&ai)[3], bool ok)
 {
     const float dx = J.x - oi.x, dy = J.y - oi.y, dz = J.z - oi.z;
@@ -101,7 +108,7 @@ __device__ __forceinline__ void pair_sym(JRec &J, const float4 &oi, const PairCo
     const float q = fmaf(fmaf(fmaf(fmaf(fmaf(K.nc[5], se, K.nc[4]), se, K.nc[3]), se, K.nc[2]), se, K.nc[1]), se,
                          K.nc[0]);
     const float f = fmaf(t2, t, q);
-    const float gi = f * J.m, gj = -f * oi.w;
+    const float gi = EQ ? f : f * J.m, gj = EQ ? f : -f * oi.w;
     if constexpr (MASKED) {
         asm("{\n\t.reg .pred p, q;\n\tsetp.lt.f32 p, %6, %7;\n\tsetp.ne.s32 q, %13, 0;\n\tand.pred p, p, q;\n\t"
             "@p fma.rn.f32 %0, %8, %10, %0;\n\t@p fma.rn.f32 %1, %8, %11, %1;\n\t@p fma.rn.f32 %2, %8, %12, %2;\n\t"
@@ -121,7 +128,7 @@ __device__ __forceinline__ void pair_sym(JRec &J, const float4 &oi, const PairCo
 // (l + k) mod 32.  UPPER bit u: i set u meets only j with a larger in-block
 // index (k >= 1 and l + k <= 31: the block of a chunk meeting itself); SKIP
 // bit u: i set u meets none of this block (j < i for all of them).
-template <int IPL, unsigned UPPER, unsigned SKIP>
+template <int IPL, unsigned UPPER, unsigned SKIP, bool EQ>
 __device__ __forceinline__ void rotate_block(JRec &J, const float4 (&oi)[IPL], const PairConsts &K,
                                              float (&ai)[IPL][3], int lane)
 {
@@ -134,22 +141,29 @@ __device__ __forceinline__ void rotate_block(JRec &J, const float4 (&oi)[IPL], c
         for (int u = 0; u < IPL; ++u) {
             if ((SKIP >> u) & 1u) continue;
             if ((UPPER >> u) & 1u)
-                pair_sym<true>(J, oi[u], K, ai[u], upper_ok);
+                pair_sym<true, EQ>(J, oi[u], K, ai[u], upper_ok);
             else
-                pair_sym<false>(J, oi[u], K, ai[u], true);
+                pair_sym<false, EQ>(J, oi[u], K, ai[u], true);
         }
-        rotate_one(J, src);
+        rotate_one<EQ>(J, src);
     }
 }
 
 // After a block: add the j partial sums to the float64 totals (skipped for
-// a j that met no i inside the cutoff).
+// a j that met no i inside the cutoff); equal masses: times -m_j.
+template <bool EQ>
 __device__ __forceinline__ void flush_j(const JRec &J, double *acc, int64_t N)
 {
     if (J.slot < 0 || (J.fx == 0.0f && J.fy == 0.0f && J.fz == 0.0f)) return;
-    atomicAdd(acc + J.slot, (double)J.fx);
-    atomicAdd(acc + N + J.slot, (double)J.fy);
-    atomicAdd(acc + 2 * N + J.slot, (double)J.fz);
+    if constexpr (EQ) {
+        atomicAdd(acc + J.slot, (double)(-J.m * J.fx));
+        atomicAdd(acc + N + J.slot, (double)(-J.m * J.fy));
+        atomicAdd(acc + 2 * N + J.slot, (double)(-J.m * J.fz));
+    } else {
+        atomicAdd(acc + J.slot, (double)J.fx);
+        atomicAdd(acc + N + J.slot, (double)J.fy);
+        atomicAdd(acc + 2 * N + J.slot, (double)J.fz);
+    }
 }
 
 // i sums of a task: float32 within a staged tile, folded into a compensated
@@ -213,19 +227,19 @@ struct AccI {
 
 // The chunk against itself, block B: its i set B held as j.  Set B meets it
 // above the diagonal (j > i), sets below B meet all of it, sets above none.
-template <int IPL, int B>
+template <int IPL, int B, bool EQ>
 __device__ __forceinline__ void diag_block(const float4 (&oi)[IPL], const bool (&active)[IPL], int ib,
                                            const PairConsts &K, AccI<IPL> &A, double *acc, int64_t N, int lane)
 {
     constexpr unsigned SKIP = ((1u << IPL) - 1u) & ~((2u << B) - 1u);
     JRec J{oi[B].x, oi[B].y, oi[B].z, oi[B].w, 0.f, 0.f, 0.f, active[B] ? ib + 32 * B + lane : -1};
-    rotate_block<IPL, (1u << B), SKIP>(J, oi, K, A.a, lane);
-    flush_j(J, acc, N);
+    rotate_block<IPL, (1u << B), SKIP, EQ>(J, oi, K, A.a, lane);
+    flush_j<EQ>(J, acc, N);
 }
 
 // One task: i particles [ib, ie) of cell c against their own chunk (j > i),
 // the rest of the cell, and the forward half of the cell's list.
-template <int JT, int STAGES, int IPL>
+template <int JT, int STAGES, int IPL, bool EQ>
 __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STAGES> &ring, float *comp, double *acc,
                                              int64_t N, int lane, int c, int ib, int ie, const hacc_volume &vol)
 {
@@ -246,11 +260,11 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
     AccI<IPL> A(comp, lane);
 
     // the chunk against itself: block B holds the chunk's i set B as j
-    diag_block<IPL, 0>(oi, active, ib, K, A, acc, N, lane);
-    if constexpr (IPL > 1) diag_block<IPL, 1>(oi, active, ib, K, A, acc, N, lane);
+    diag_block<IPL, 0, EQ>(oi, active, ib, K, A, acc, N, lane);
+    if constexpr (IPL > 1) diag_block<IPL, 1, EQ>(oi, active, ib, K, A, acc, N, lane);
     if constexpr (IPL > 2) {
-        diag_block<IPL, 2>(oi, active, ib, K, A, acc, N, lane);
-        diag_block<IPL, 3>(oi, active, ib, K, A, acc, N, lane);
+        diag_block<IPL, 2, EQ>(oi, active, ib, K, A, acc, N, lane);
+        diag_block<IPL, 3, EQ>(oi, active, ib, K, A, acc, N, lane);
     }
     A.fold();
 
@@ -323,8 +337,8 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
                     at += take;
                     oo += take;
                 }
-                rotate_block<IPL, 0u, 0u>(J, oi, K, A.a, lane);
-                flush_j(J, acc, N);
+                rotate_block<IPL, 0u, 0u, EQ>(J, oi, K, A.a, lane);
+                flush_j<EQ>(J, acc, N);
             }
             A.fold();
             ++ring.consumed;
@@ -336,9 +350,16 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
     for (int u = 0; u < IPL; ++u) {
         if (!active[u]) continue;
         const int i = ib + lane + 32 * u;
-        atomicAdd(acc + i, A.total(u, 0));
-        atomicAdd(acc + N + i, A.total(u, 1));
-        atomicAdd(acc + 2 * N + i, A.total(u, 2));
+        if constexpr (EQ) {
+            const double m = (double)oi[u].w;
+            atomicAdd(acc + i, m * A.total(u, 0));
+            atomicAdd(acc + N + i, m * A.total(u, 1));
+            atomicAdd(acc + 2 * N + i, m * A.total(u, 2));
+        } else {
+            atomicAdd(acc + i, A.total(u, 0));
+            atomicAdd(acc + N + i, A.total(u, 1));
+            atomicAdd(acc + 2 * N + i, A.total(u, 2));
+        }
     }
     return true;
 }
@@ -350,9 +371,14 @@ __host__ __device__ constexpr int sym_warp_smem_bytes(int jt, int stages)
     return (warp_tiles_bytes(FORCE, jt, stages) + SYM_COMP_BYTES + stages * 8 + 127) / 128 * 128;
 }
 
-template <int JT, int STAGES>
+// EQ: the equal-mass instantiation.  Both are launched when the binning
+// checked the masses, and the one that does not match the flag returns at
+// once; each keeps its own register allocation.
+template <int JT, int STAGES, bool EQ>
 __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc, int64_t N)
 {
+    const bool eq = a.mass_varies && *a.mass_varies == 0u;
+    if (eq != EQ) return;
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int WARP_BYTES = sym_warp_smem_bytes(JT, STAGES);
     constexpr int TILE_BYTES = warp_tiles_bytes(FORCE, JT, STAGES);
@@ -379,11 +405,11 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc
         bool ok;
         const int size = task.z - task.y;
         if (size > 64)
-            ok = run_task_sym<JT, STAGES, 4>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+            ok = run_task_sym<JT, STAGES, 4, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         else if (size > 32)
-            ok = run_task_sym<JT, STAGES, 2>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+            ok = run_task_sym<JT, STAGES, 2, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         else
-            ok = run_task_sym<JT, STAGES, 1>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+            ok = run_task_sym<JT, STAGES, 1, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();
@@ -405,11 +431,11 @@ k_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restric
     }
 }
 
-template <int JT, int STAGES>
-int launch_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
+template <int JT, int STAGES, bool EQ>
+int launch_sym_one(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
 {
     const size_t smem = (size_t)warps * sym_warp_smem_bytes(JT, STAGES);
-    auto kern = k_pairs_sym<JT, STAGES>;
+    auto kern = k_pairs_sym<JT, STAGES, EQ>;
     if (smem > 48 * 1024)
         HACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -419,6 +445,16 @@ int launch_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per
     kern<<<num_sms() * per_sm, warps * 32, smem, st>>>(a, acc, N);
     HACC_LAUNCH_CHECK();
     return HACC_OK;
+}
+
+template <int JT, int STAGES>
+int launch_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
+{
+    if (a.mass_varies) {
+        const int rc = launch_sym_one<JT, STAGES, true>(a, acc, N, warps, ctas_per_sm, st);
+        if (rc) return rc;
+    }
+    return launch_sym_one<JT, STAGES, false>(a, acc, N, warps, ctas_per_sm, st);
 }
 
 int launch_sym(const KArgs &a, double *acc, int64_t N, const hacc_launch &L, cudaStream_t st)
@@ -452,13 +488,13 @@ struct JAdj {
     int slot;
 };
 
-template <bool GM>
+template <bool GM, bool EQ>
 __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
 {
     J.x = __shfl_sync(FULL, J.x, src);
     J.y = __shfl_sync(FULL, J.y, src);
     J.z = __shfl_sync(FULL, J.z, src);
-    J.m = __shfl_sync(FULL, J.m, src);
+    if constexpr (!EQ) J.m = __shfl_sync(FULL, J.m, src);
     J.lx = __shfl_sync(FULL, J.lx, src);
     J.ly = __shfl_sync(FULL, J.ly, src);
     J.lz = __shfl_sync(FULL, J.lz, src);
@@ -474,8 +510,9 @@ __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
 
 // One pair of the adjoint, both sides; outside the cutoff (or outside the
 // upper triangle of a diagonal block) f and r are zero, so every sum is
-// unchanged.
-template <bool GM>
+// unchanged.  Equal masses (EQ): V sums f on both sides and r = fp2
+// d.(lam_j - lam_i), the common mass applied by the finishing pass.
+template <bool GM, bool EQ>
 __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const float4 &li, const PairConsts &K,
                                              float (&acc)[ADJ_NACC], bool ok)
 {
@@ -492,12 +529,20 @@ __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const fl
     const float dli = fmaf(dz, li.z, fmaf(dy, li.y, dx * li.x));
     const bool in = ok & (se < K.rc2e);
     const float f = in ? t3 + q : 0.0f;
-    const float r = in ? fp2 * fmaf(oi.w, dlj, -(J.m * dli)) : 0.0f;
+    float rr;
+    if constexpr (EQ && !GM)
+        rr = fp2 * fmaf(dz, J.lz - li.z, fmaf(dy, J.ly - li.y, dx * (J.lx - li.x)));
+    else if constexpr (EQ)
+        rr = fp2 * (dlj - dli);
+    else
+        rr = fp2 * fmaf(oi.w, dlj, -(J.m * dli));
+    const float r = in ? rr : 0.0f;
+    const float mj = EQ ? 1.0f : J.m, mi = EQ ? 1.0f : oi.w;
     // i side
     acc[0] = fmaf(f, J.lx, acc[0]);
     acc[1] = fmaf(f, J.ly, acc[1]);
     acc[2] = fmaf(f, J.lz, acc[2]);
-    acc[3] = fmaf(J.m, f, acc[3]);
+    acc[3] = fmaf(mj, f, acc[3]);
     acc[4] = fmaf(r, dx, acc[4]);
     acc[5] = fmaf(r, dy, acc[5]);
     acc[6] = fmaf(r, dz, acc[6]);
@@ -506,14 +551,14 @@ __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const fl
     J.u0 = fmaf(f, li.x, J.u0);
     J.u1 = fmaf(f, li.y, J.u1);
     J.u2 = fmaf(f, li.z, J.u2);
-    J.v = fmaf(oi.w, f, J.v);
+    J.v = fmaf(mi, f, J.v);
     J.x0 = fmaf(-r, dx, J.x0);
     J.x1 = fmaf(-r, dy, J.x1);
     J.x2 = fmaf(-r, dz, J.x2);
     if constexpr (GM) J.g = fmaf(-f, dli, J.g);
 }
 
-template <int IPL, bool GM, unsigned UPPER, unsigned SKIP>
+template <int IPL, bool GM, bool EQ, unsigned UPPER, unsigned SKIP>
 __device__ __forceinline__ void rotate_block_adj(JAdj &J, const float4 (&oi)[IPL], const float4 (&li)[IPL],
                                                  const PairConsts &K, float (&p)[IPL][ADJ_NACC], int lane)
 {
@@ -524,9 +569,9 @@ __device__ __forceinline__ void rotate_block_adj(JAdj &J, const float4 (&oi)[IPL
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
             if ((SKIP >> u) & 1u) continue;
-            pair_adj_sym<GM>(J, oi[u], li[u], K, p[u], ((UPPER >> u) & 1u) ? upper_ok : true);
+            pair_adj_sym<GM, EQ>(J, oi[u], li[u], K, p[u], ((UPPER >> u) & 1u) ? upper_ok : true);
         }
-        rotate_adj<GM>(J, src);
+        rotate_adj<GM, EQ>(J, src);
     }
 }
 
@@ -543,7 +588,7 @@ __device__ __forceinline__ void flush_adj(const JAdj &J, double *acc, int64_t N)
     for (int k = 0; k < (GM ? 8 : 7); ++k) atomicAdd(acc + k * N + J.slot, (double)c[k]);
 }
 
-template <int JT, int STAGES, int IPL, bool GM>
+template <int JT, int STAGES, int IPL, bool GM, bool EQ>
 __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, JT, STAGES> &ring, float *comp,
                                                  double *acc, int64_t N, int lane, int c, int ib, int ie,
                                                  const hacc_volume &vol)
@@ -569,12 +614,12 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
     {  // the chunk against itself
         JAdj J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, li[0].x, li[0].y, li[0].z,
                0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[0] ? ib + lane : -1};
-        rotate_block_adj<IPL, GM, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, li, K, A.p, lane);
+        rotate_block_adj<IPL, GM, EQ, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, li, K, A.p, lane);
         flush_adj<GM>(J, acc, N);
         if constexpr (IPL == 2) {
             JAdj J1{oi[1].x, oi[1].y, oi[1].z, oi[1].w, li[1].x, li[1].y, li[1].z,
                     0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[1] ? ib + 32 + lane : -1};
-            rotate_block_adj<IPL, GM, 2u, 0u>(J1, oi, li, K, A.p, lane);
+            rotate_block_adj<IPL, GM, EQ, 2u, 0u>(J1, oi, li, K, A.p, lane);
             flush_adj<GM>(J1, acc, N);
         }
         A.fold();
@@ -649,7 +694,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
                     at += take;
                     oo += take;
                 }
-                rotate_block_adj<IPL, GM, 0u, 0u>(J, oi, li, K, A.p, lane);
+                rotate_block_adj<IPL, GM, EQ, 0u, 0u>(J, oi, li, K, A.p, lane);
                 flush_adj<GM>(J, acc, N);
             }
             A.fold();
@@ -669,9 +714,11 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
     return true;
 }
 
-template <int JT, int STAGES, bool GM>
+template <int JT, int STAGES, bool GM, bool EQ>
 __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, int64_t N)
 {
+    const bool eq = a.mass_varies && *a.mass_varies == 0u;
+    if (eq != EQ) return;  // the other instantiation does the work
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int WARP_BYTES = warp_smem_bytes(ADJOINT, JT, STAGES);
     constexpr int TILE_BYTES = warp_tiles_bytes(ADJOINT, JT, STAGES);
@@ -699,9 +746,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
         for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
             const int se = min(sb + 64, task.z);
             if (se - sb > 32)
-                ok = run_task_adj_sym<JT, STAGES, 2, GM>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
+                ok = run_task_adj_sym<JT, STAGES, 2, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
             else
-                ok = run_task_adj_sym<JT, STAGES, 1, GM>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
+                ok = run_task_adj_sym<JT, STAGES, 1, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
         }
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
@@ -711,29 +758,37 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
     }
 }
 
-// dL/dx_k = m_k U - lam_k V + X and dL/dm_k = -G from the float64 totals, in input order.
+// dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V + X)) and
+// dL/dm_k = -G from the float64 totals, in input order.
 __global__ void __launch_bounds__(256)
 k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm,
-                 const float4 *__restrict__ pos, const float4 *__restrict__ lam, float *__restrict__ gx,
-                 float *__restrict__ gy, float *__restrict__ gz, float *__restrict__ gm)
+                 const float4 *__restrict__ pos, const float4 *__restrict__ lam, const uint32_t *mass_varies,
+                 float *__restrict__ gx, float *__restrict__ gy, float *__restrict__ gz, float *__restrict__ gm)
 {
+    const bool eq = mass_varies && *mass_varies == 0u;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[k];
         const double m = (double)pos[k].w;
         const float4 l = lam[k];
         const double V = acc[3 * N + k];
-        gx[i] = (float)(m * acc[k] - (double)l.x * V + acc[4 * N + k]);
-        gy[i] = (float)(m * acc[N + k] - (double)l.y * V + acc[5 * N + k]);
-        gz[i] = (float)(m * acc[2 * N + k] - (double)l.z * V + acc[6 * N + k]);
+        if (eq) {
+            gx[i] = (float)(m * (acc[k] - (double)l.x * V + acc[4 * N + k]));
+            gy[i] = (float)(m * (acc[N + k] - (double)l.y * V + acc[5 * N + k]));
+            gz[i] = (float)(m * (acc[2 * N + k] - (double)l.z * V + acc[6 * N + k]));
+        } else {
+            gx[i] = (float)(m * acc[k] - (double)l.x * V + acc[4 * N + k]);
+            gy[i] = (float)(m * acc[N + k] - (double)l.y * V + acc[5 * N + k]);
+            gz[i] = (float)(m * acc[2 * N + k] - (double)l.z * V + acc[6 * N + k]);
+        }
         if (gm) gm[i] = (float)(-acc[7 * N + k]);
     }
 }
 
-template <int JT, int STAGES, bool GM>
-int launch_adj_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
+template <int JT, int STAGES, bool GM, bool EQ>
+int launch_adj_sym_one(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
 {
     const size_t smem = (size_t)warps * warp_smem_bytes(ADJOINT, JT, STAGES);
-    auto kern = k_adj_sym<JT, STAGES, GM>;
+    auto kern = k_adj_sym<JT, STAGES, GM, EQ>;
     if (smem > 48 * 1024)
         HACC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -743,6 +798,16 @@ int launch_adj_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas
     kern<<<num_sms() * per_sm, warps * 32, smem, st>>>(a, acc, N);
     HACC_LAUNCH_CHECK();
     return HACC_OK;
+}
+
+template <int JT, int STAGES, bool GM>
+int launch_adj_sym_t(const KArgs &a, double *acc, int64_t N, int warps, int ctas_per_sm, cudaStream_t st)
+{
+    if (a.mass_varies) {
+        const int rc = launch_adj_sym_one<JT, STAGES, GM, true>(a, acc, N, warps, ctas_per_sm, st);
+        if (rc) return rc;
+    }
+    return launch_adj_sym_one<JT, STAGES, GM, false>(a, acc, N, warps, ctas_per_sm, st);
 }
 
 template <bool GM>
@@ -828,7 +893,7 @@ extern "C" int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc
     rc = gm ? launch_adj_sym<true>(a, F.acc, mesh->N, L, st) : launch_adj_sym<false>(a, F.acc, mesh->N, L, st);
     if (rc) return rc;
     k_adj_sym_finish<<<g, 256, 0, st>>>(mesh->N, F.acc, binned->perm, reinterpret_cast<const float4 *>(binned->sorted4),
-                                        F.lam, gx, gy, gz, gm);
+                                        F.lam, binned->mass_varies, gx, gy, gz, gm);
     HACC_LAUNCH_CHECK();
     return HACC_OK;
 }

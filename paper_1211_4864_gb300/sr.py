@@ -216,12 +216,15 @@ class ShortRange:
 
     def __init__(self, L, vol_off, rcut: float, cell_min: float | None = None, split_T: int = 32,
                  device: str | torch.device = "cuda", builder: str = "mesh", leaf_max: int = 64,
-                 max_depth: int = 48, skin: float = 0.0):
+                 max_depth: int = 48, skin: float = 0.0, equal_mass_path: bool = True):
         """builder: "mesh" (chaining mesh, hacc_bin + hacc_build_lists) or "rcb"
         (the paper's RCB fat-leaf tree, hacc_rcb_build + hacc_rcb_lists, leaves
         of at most leaf_max particles; its build synchronises the stream).
         skin (mesh only): lists built for rcut + skin, so that binned particles
-        may drift up to skin/2 (drift_offsets) before the next binning."""
+        may drift up to skin/2 (drift_offsets) before the next binning.
+        equal_mass_path: let the binning flag equal masses (hacc_binned
+        mass_varies) so that the force calls take their equal-mass path;
+        False passes no flag and always runs the general path."""
         if builder not in ("mesh", "rcb"):
             raise HaccError(f"unknown list builder {builder!r}")
         if skin < 0 or (skin > 0 and builder != "mesh"):
@@ -249,10 +252,11 @@ class ShortRange:
         self.split_T = int(split_T)
         self.n_tasks = torch.zeros(1, dtype=i32, device=dev)
         self.n_pairs = torch.zeros(1, dtype=i64, device=dev)
+        self.mass_varies = torch.ones(1, dtype=i32, device=dev) if equal_mass_path else None
         if builder == "mesh":
             self.cell_start = torch.empty(self.n_cells + 1, dtype=i32, device=dev)
             self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.cell_start), _ptr(self.perm),
-                                      _ptr(self.sorted4), None)
+                                      _ptr(self.sorted4), None, _ptr(self.mass_varies))
             self.task_cap = int(lib.hacc_task_capacity(ctypes.byref(self.mesh), self.split_T))
             self.nbr_off = torch.empty(self.n_cells + 1, dtype=i64, device=dev)
             self.entry_cap = self.n_entries
@@ -273,7 +277,7 @@ class ShortRange:
                                   _ptr(self.leaf_start), _ptr(self.leaf_qbox), _ptr(self.leaf_origin),
                                   _ptr(self.node_qbox), _ptr(self.node_child), _ptr(self.root))
             self.binned = hacc_binned(_ptr(self.cell_of), _ptr(self.leaf_start), _ptr(self.perm),
-                                      _ptr(self.sorted4), _ptr(self.leaf_origin))
+                                      _ptr(self.sorted4), _ptr(self.leaf_origin), _ptr(self.mass_varies))
             # each leaf gives ceil(size / T) tasks
             self.task_cap = lc + N // self.split_T + 1
             self.nbr_off = torch.empty(lc + 1, dtype=i64, device=dev)
@@ -428,6 +432,22 @@ class ShortRange:
             if (c + 1) % k != 0 and c + 1 < n_c:  # the next force reuses these records
                 self.drift_offsets(v, 0.5 * h)
         return a
+
+    def set_equal_mass_path(self, enabled: bool):
+        """Pass (enabled) or withhold the equal-mass flag of the binned
+        particles; from the next prepare on, the force calls take the
+        equal-mass path when every mass is equal, or the general path always."""
+        if enabled and self.mass_varies is None:
+            self.mass_varies = torch.ones(1, dtype=torch.int32, device=self.device)
+        elif enabled:
+            self.mass_varies.fill_(1)
+        self.binned.mass_varies = _ptr(self.mass_varies) if enabled else None
+
+    @property
+    def equal_mass(self) -> bool:
+        """True when the last binning found every mass equal (the force calls
+        then take the equal-mass path); reads the device flag."""
+        return self.binned.mass_varies is not None and int(self.mass_varies.item()) == 0
 
     def prepare(self, pos, m, disp=None):
         """Binning and lists for positions pos [3, N] (plus displacements disp

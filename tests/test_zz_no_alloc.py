@@ -28,7 +28,7 @@ def _run(hs, torch, w, noalloc):
         hs.hacc_bin(sr.mesh, pos[0], pos[1], pos[2], m, sr.binned, sr.ws, sr.status)
     torch.cuda.synchronize()
     assert int(sr.status.item()) == 0
-    return [t.cpu().numpy().copy() for t in (sr.cell_of, sr.cell_start, sr.perm, sr.sorted4)]
+    return [t.cpu().numpy().copy() for t in (sr.cell_of, sr.cell_start, sr.perm, sr.sorted4, sr.mass_varies)]
 
 
 @pytest.mark.gpu
@@ -38,8 +38,11 @@ def test_noalloc_binning_matches_workspace_binning_twice():
         pytest.skip("no CUDA device")
     import paper_1211_4864_gb300 as hs
     hs.load()
-    # two different problems back to back through the shared scratch array
-    for w in (clustered_box(24, 6, seed=12), uniform_box(4096, 16.0, seed=1)):
+    # different problems back to back through the shared scratch array (the last one with
+    # varied masses: the equal-mass flag set, as by hacc_bin)
+    varied = uniform_box(3000, 14.0, seed=4)
+    varied.m[:] = np.random.default_rng(4).uniform(0.5, 2.0, varied.N).astype(np.float32)
+    for w in (clustered_box(24, 6, seed=12), uniform_box(4096, 16.0, seed=1), varied):
         got = _run(hs, torch, w, noalloc=True)
         ref = _run(hs, torch, w, noalloc=False)
         for g, r in zip(got, ref):

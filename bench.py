@@ -42,12 +42,12 @@ FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
 # ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
 # they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2221974272 + 966593024,
+    "gather": {"workload": "clustered256", "bytes": 2219115264 + 966378752,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "4907fe99d6391d9aaa1359748f060e716cd402fd7c1ea9e0a3aa8a98fa423662"},
-    "symmetric": {"workload": "clustered256", "bytes": 2817565440 + 1504486144,
+               "sha256": "40962c6002c7f1679c570ca48baf21394977c86d52b4064efecc1ff3f93eaf95"},
+    "symmetric": {"workload": "clustered256", "bytes": 2819386624 + 1505460224,
                   "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
-                  "sha256": "adad5997e885e37902084014fac552b49c023a0767fc82c3a70a380775e26c94"},
+                  "sha256": "f6f9354ac5a3eb57b64ec4d00229e2518480f44733cb2c42627ef63943504be9"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

@@ -124,19 +124,23 @@ __device__ __forceinline__ void pair_sym(JRec &J, const float4 &oi, const PairCo
     }
 }
 
-// 32 rotation steps: at step k lane l holds the j that started in lane
-// (l + k) mod 32.  UPPER bit u: i set u meets only j with a larger in-block
-// index (k >= 1 and l + k <= 31: the block of a chunk meeting itself); SKIP
-// bit u: i set u meets none of this block (j < i for all of them).
-template <int IPL, unsigned UPPER, unsigned SKIP, bool EQ>
+// W rotation steps within groups of W lanes (W = 32: the whole warp; W = 16:
+// each half-warp rotates its own 16 records): at step k lane l holds the j
+// that started in lane g + (l - g + k) mod W of its group g.  UPPER bit u: i
+// set u meets only j with a larger in-group index (k >= 1 and (l - g) + k <=
+// W - 1: the block of a chunk meeting itself); SKIP bit u: i set u meets none
+// of this block (j < i for all of them).
+template <int IPL, unsigned UPPER, unsigned SKIP, bool EQ, int W = 32>
 __device__ __forceinline__ void rotate_block(JRec &J, const float4 (&oi)[IPL], const PairConsts &K,
                                              float (&ai)[IPL][3], int lane)
 {
-    const int src = (lane + 1) & 31;
+    static_assert(W == 32 || W == 16, "rotation width");
+    const int src = (lane & (32 - W)) | ((lane + 1) & (W - 1));
+    const int lg = lane & (W - 1);
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        // k >= 1 and lane + k <= 31, without short-circuit branches
-        const bool upper_ok = (k != 0) & (lane + k < 32);
+    for (int k = 0; k < W; ++k) {
+        // k >= 1 and lg + k <= W - 1, without short-circuit branches
+        const bool upper_ok = (k != 0) & (lg + k < W);
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
             if ((SKIP >> u) & 1u) continue;
@@ -237,12 +241,31 @@ __device__ __forceinline__ void diag_block(const float4 (&oi)[IPL], const bool (
     flush_j<EQ>(J, acc, N);
 }
 
+// Half-warp tasks (at most 16 particles, i = lane mod 16 in both halves):
+// the chunk against itself on the low half only (16 steps, upper triangle);
+// the high half holds no i and no j for this block.
+template <bool EQ>
+__device__ __forceinline__ void diag_block_half(const float4 (&oi)[1], bool active, int ib, const PairConsts &K,
+                                                AccI<1> &A, double *acc, int64_t N, int lane)
+{
+    const float4 od[1] = {lane < 16 ? oi[0] : make_float4(FAR, FAR, FAR, 0.f)};
+    JRec J{od[0].x, od[0].y, od[0].z, od[0].w, 0.f, 0.f, 0.f, (lane < 16 && active) ? ib + lane : -1};
+    rotate_block<1, 1u, 0u, EQ, 16>(J, od, K, A.a, lane);
+    flush_j<EQ>(J, acc, N);
+}
+
 // One task: i particles [ib, ie) of cell c against their own chunk (j > i),
-// the rest of the cell, and the forward half of the cell's list.
-template <int JT, int STAGES, int IPL, bool EQ>
+// the rest of the cell, and the forward half of the cell's list.  HALF (one
+// i set of at most 16): every i sits in lane l and lane l + 16, and the two
+// half-warps rotate the two halves of each block of 32 j, so that all 32
+// lanes work and each pair is still met once.
+template <int JT, int STAGES, int IPL, bool EQ, bool HALF = false>
 __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STAGES> &ring, float *comp, double *acc,
                                              int64_t N, int lane, int c, int ib, int ie, const hacc_volume &vol)
 {
+    static_assert(!HALF || IPL == 1, "half-warp tasks hold one i set");
+    constexpr int W = HALF ? 16 : 32;
+    const int il = HALF ? (lane & 15) : lane;  // this lane's i within its set
     const PairConsts &K = a.k;
     const int n = vol.n;
     const int64_t lc = (int64_t)c - vol.cell_base;
@@ -253,14 +276,18 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
     bool active[IPL];
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        const int i = ib + lane + 32 * u;
+        const int i = ib + il + 32 * u;
         active[u] = i < ie;
         oi[u] = active[u] ? a.pos[i] : make_float4(FAR, FAR, FAR, 0.f);
     }
     AccI<IPL> A(comp, lane);
 
     // the chunk against itself: block B holds the chunk's i set B as j
-    diag_block<IPL, 0, EQ>(oi, active, ib, K, A, acc, N, lane);
+    if constexpr (HALF) {
+        diag_block_half<EQ>(oi, active[0], ib, K, A, acc, N, lane);
+    } else {
+        diag_block<IPL, 0, EQ>(oi, active, ib, K, A, acc, N, lane);
+    }
     if constexpr (IPL > 1) diag_block<IPL, 1, EQ>(oi, active, ib, K, A, acc, N, lane);
     if constexpr (IPL > 2) {
         diag_block<IPL, 2, EQ>(oi, active, ib, K, A, acc, N, lane);
@@ -337,7 +364,7 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
                     at += take;
                     oo += take;
                 }
-                rotate_block<IPL, 0u, 0u, EQ>(J, oi, K, A.a, lane);
+                rotate_block<IPL, 0u, 0u, EQ, W>(J, oi, K, A.a, lane);
                 flush_j<EQ>(J, acc, N);
             }
             A.fold();
@@ -349,7 +376,7 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
         if (!active[u]) continue;
-        const int i = ib + lane + 32 * u;
+        const int i = ib + il + 32 * u;  // HALF: both lanes of i add their part
         if constexpr (EQ) {
             const double m = (double)oi[u].w;
             atomicAdd(acc + i, m * A.total(u, 0));
@@ -408,8 +435,10 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc
             ok = run_task_sym<JT, STAGES, 4, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         else if (size > 32)
             ok = run_task_sym<JT, STAGES, 2, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
-        else
+        else if (size > 16)
             ok = run_task_sym<JT, STAGES, 1, EQ>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
+        else
+            ok = run_task_sym<JT, STAGES, 1, EQ, true>(a, ring, comp, acc, N, lane, task.x, task.y, task.z, vol);
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);
             ring.drain();

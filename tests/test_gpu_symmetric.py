@@ -51,8 +51,8 @@ def oracle_force(w: Workload, v=0, targets=None):
     return oracle.sr_force(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), EPS, RC, c, targets)
 
 
-@pytest.mark.parametrize("case", ["uniform", "clustered", "fine_mesh", "small_box", "tiny_tasks", "tasks128",
-                                  "tasks100"])
+@pytest.mark.parametrize("case", ["uniform", "clustered", "fine_mesh", "small_box", "tiny_tasks", "tasks16",
+                                  "tasks128", "tasks100"])
 def test_symmetric_against_oracle_and_gather(hs, case):
     cell_min, split_T = None, 64
     if case == "uniform":
@@ -65,6 +65,8 @@ def test_symmetric_against_oracle_and_gather(hs, case):
         w = uniform_box(1500, 9.0, seed=19)
     elif case == "tiny_tasks":  # chunks of 7 particles: many tasks per cell, every diagonal block ragged
         w, split_T = clustered_box(16, 3, seed=22), 7
+    elif case == "tasks16":  # chunks of 16: every task on the half-warp rotation, full halves
+        w, split_T = clustered_box(18, 4, seed=24), 16
     elif case == "tasks128":  # four i per lane in the symmetric kernel, 64-particle sub-chunks in the gather
         w, split_T = clustered_box(20, 4, seed=25), 128
     else:  # 100-particle chunks: the fourth i set partly empty

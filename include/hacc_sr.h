@@ -119,8 +119,9 @@ typedef struct hacc_lists {
                             cost class (particles x list length, power-of-two classes), stable */
     int64_t task_cap;  /* capacity of `tasks`, in tasks */
     int32_t split_T;   /* a task holds at most split_T particles of one cell; the pair calls take
-                          1..128 (one, two or four i particles per lane in the symmetric force
-                          kernel; the other pair kernels walk a task in 64-particle sub-chunks) */
+                          1..128 (the symmetric force kernel runs a task of at most 16 particles
+                          on two half-warps, then one, two or four i particles per lane; the
+                          other pair kernels walk a task in 64-particle sub-chunks) */
     int32_t pad;
 } hacc_lists;
 

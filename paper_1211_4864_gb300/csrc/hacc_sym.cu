@@ -95,10 +95,11 @@ __device__ __forceinline__ void rotate_block(JRec &J, const float4 (&oi)[IPL], c
     static_assert(W == 32 || W == 16, "rotation width");
     const int src = (lane & (32 - W)) | ((lane + 1) & (W - 1));
     const int lg = lane & (W - 1);
+    const bool rows = W == 32 || UPPER == 0u || lane < 16;  // a half-warp task's own block: low half only
 #pragma unroll 4
     for (int k = 0; k < W; ++k) {
         // k >= 1 and lg + k <= W - 1, without short-circuit branches
-        const bool upper_ok = (k != 0) & (lg + k < W);
+        const bool upper_ok = (k != 0) & (lg + k < W) & rows;
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
             if ((SKIP >> u) & 1u) continue;

@@ -97,14 +97,20 @@ __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const fl
     if constexpr (GM) J.g = fmaf(-f, dli, J.g);
 }
 
-template <int IPL, bool GM, bool EQ, unsigned UPPER, unsigned SKIP>
+// W rotation steps within groups of W lanes, as the force kernel's
+// rotate_block; a half-warp block with an UPPER set (the chunk's own block of
+// a half-warp task) pairs on the low half only.
+template <int IPL, bool GM, bool EQ, unsigned UPPER, unsigned SKIP, int W = 32>
 __device__ __forceinline__ void rotate_block_adj(JAdj &J, const float4 (&oi)[IPL], const float4 (&li)[IPL],
                                                  const PairConsts &K, float (&p)[IPL][ADJ_NACC], int lane)
 {
-    const int src = (lane + 1) & 31;
+    static_assert(W == 32 || W == 16, "rotation width");
+    const int src = (lane & (32 - W)) | ((lane + 1) & (W - 1));
+    const int lg = lane & (W - 1);
+    const bool rows = W == 32 || UPPER == 0u || lane < 16;
 #pragma unroll 2
-    for (int k = 0; k < 32; ++k) {
-        const bool upper_ok = (k != 0) & (lane + k < 32);
+    for (int k = 0; k < W; ++k) {
+        const bool upper_ok = (k != 0) & (lg + k < W) & rows;
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
             if ((SKIP >> u) & 1u) continue;
@@ -127,11 +133,18 @@ __device__ __forceinline__ void flush_adj(const JAdj &J, double *acc, int64_t N)
     for (int k = 0; k < (GM ? 8 : 7); ++k) atomicAdd(acc + k * N + J.slot, (double)c[k]);
 }
 
-template <int JT, int STAGES, int IPL, bool GM, bool EQ>
+// One task (sub-chunk): i particles [ib, ie) against their own chunk, the
+// rest of the cell and the forward half of the list.  HALF (at most 16
+// particles): each i in lanes l and l + 16, the half-warps rotate the two
+// halves of each block of 32 j (as the force kernel).
+template <int JT, int STAGES, int IPL, bool GM, bool EQ, bool HALF = false>
 __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, JT, STAGES> &ring, float *comp,
                                                  double *acc, int64_t N, int lane, int c, int ib, int ie,
                                                  const hacc_volume &vol)
 {
+    static_assert(!HALF || IPL == 1, "half-warp tasks hold one i set");
+    constexpr int W = HALF ? 16 : 32;
+    const int il = HALF ? (lane & 15) : lane;
     constexpr int MODE = GM ? ADJOINT_GM : ADJOINT;
     const PairConsts &K = a.k;
     const int n = vol.n;
@@ -143,14 +156,25 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
     bool active[IPL];
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        const int i = ib + lane + 32 * u;
+        const int i = ib + il + 32 * u;
         active[u] = i < ie;
         oi[u] = active[u] ? a.pos[i] : make_float4(FAR, FAR, FAR, 0.f);
         li[u] = active[u] ? a.lam[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     AccAdj<MODE, IPL> A(comp, lane);
 
-    {  // the chunk against itself
+    if constexpr (HALF) {  // the chunk against itself on the low half-warp, 16 steps
+        const bool lo = lane < 16;
+        JAdj J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, li[0].x, li[0].y, li[0].z,
+               0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, (lo && active[0]) ? ib + lane : -1};
+        if (!lo) {
+            J.x = J.y = J.z = FAR;
+            J.m = J.lx = J.ly = J.lz = 0.f;
+        }
+        rotate_block_adj<1, GM, EQ, 1u, 0u, 16>(J, oi, li, K, A.p, lane);
+        flush_adj<GM>(J, acc, N);
+        A.fold();
+    } else {  // the chunk against itself
         JAdj J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, li[0].x, li[0].y, li[0].z,
                0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[0] ? ib + lane : -1};
         rotate_block_adj<IPL, GM, EQ, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, li, K, A.p, lane);
@@ -233,7 +257,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
                     at += take;
                     oo += take;
                 }
-                rotate_block_adj<IPL, GM, EQ, 0u, 0u>(J, oi, li, K, A.p, lane);
+                rotate_block_adj<IPL, GM, EQ, 0u, 0u, W>(J, oi, li, K, A.p, lane);
                 flush_adj<GM>(J, acc, N);
             }
             A.fold();
@@ -245,7 +269,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
         if (!active[u]) continue;
-        const int i = ib + lane + 32 * u;
+        const int i = ib + il + 32 * u;  // HALF: both lanes of i add their part
 #pragma unroll
         for (int k = 0; k < (GM ? 8 : 7); ++k)
             atomicAdd(acc + k * N + i, (double)A.hi(u, k) + (double)A.lo(u, k));
@@ -286,8 +310,11 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
             const int se = min(sb + 64, task.z);
             if (se - sb > 32)
                 ok = run_task_adj_sym<JT, STAGES, 2, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
-            else
+            else if (se - sb > 16)
                 ok = run_task_adj_sym<JT, STAGES, 1, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
+            else
+                ok = run_task_adj_sym<JT, STAGES, 1, GM, EQ, true>(a, ring, comp, acc, N, lane, task.x, sb, se,
+                                                                   vol);
         }
         if (!ok) {
             if (lane == 0) atomicOr(a.status, HACC_STATUS_TIMEOUT);

@@ -42,12 +42,12 @@ FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
 # ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
 # they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2219115264 + 966378752,
+    "gather": {"workload": "clustered256", "bytes": 2221459456 + 966782208,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
                "sha256": "40962c6002c7f1679c570ca48baf21394977c86d52b4064efecc1ff3f93eaf95"},
-    "symmetric": {"workload": "clustered256", "bytes": 2819386624 + 1505460224,
-                  "sources": ["hacc_sym.cu", "hacc_pairs.cuh"],
-                  "sha256": "f6f9354ac5a3eb57b64ec4d00229e2518480f44733cb2c42627ef63943504be9"},
+    "symmetric": {"workload": "clustered256", "bytes": 2793387264 + 1488423680,
+                  "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
+                  "sha256": "fd448cf8dbca355f7bac05b4940cc4358f8d28b63c61d8ba10fff9093c2c9003"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
@@ -925,9 +925,11 @@ def sweep(args):
             sr.prepare(pos, m)
             torch.cuda.synchronize()
             pairs = sr.pair_count()
+            eq = sr.equal_mass  # unit masses: the equal-mass path, and its executed flops
             out = torch.empty((3, n), device="cuda")
-            for kernel, fn, flops in (("gather", sr.force, FLOPS_PER_PAIR * pairs),
-                                      ("symmetric", sr.force_symmetric, FLOPS_PER_SYM_PAIR * pairs / 2)):
+            for kernel, fn, flops in (("gather", sr.force, (FLOPS_PER_PAIR_EQ if eq else FLOPS_PER_PAIR) * pairs),
+                                      ("symmetric", sr.force_symmetric,
+                                       (FLOPS_PER_SYM_PAIR_EQ if eq else FLOPS_PER_SYM_PAIR) * pairs / 2)):
                 for cps in (1, 2, 3):
                     L = hs.Launch(8, cps, 128, 2)
                     fn(prm, out, launch=L)
@@ -940,6 +942,7 @@ def sweep(args):
                     torch.cuda.synchronize()
                     t = e0.elapsed_time(e1) / 5
                     rows.append({"density": rho, "list_length": pairs / n, "split_T": T, "kernel": kernel,
+                                 "mass_path": "equal" if eq else "general",
                                  "ctas_per_sm": cps, "warps_per_sm": 8 * cps, "ms": t,
                                  "interactions_per_s": pairs / (t * 1e-3),
                                  "frac_fp32_peak_executed": flops / (t * 1e-3) / peak})

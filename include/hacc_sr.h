@@ -405,11 +405,17 @@ int hacc_drift_offsets(const hacc_mesh *mesh, const hacc_binned *binned, const f
 /* Bytes of scratch that hacc_moments needs. */
 size_t hacc_moments_workspace_size(int64_t N);
 
-/* Global float64 reductions, in a fixed order (deterministic):
+/* Global reductions, in a fixed order (deterministic):
  *   out[0..2] = sum m v,  out[3..5] = sum m a  (zero by Newton's third law),
  *   out[6] = sum m |v|^2 / 2,  out[7] = sum m |a|,
  *   out[8] = sum m phi / 2 (the short-range potential energy; each pair once).
- * Any of v, a, phi may be NULL (its sums are then 0).  out: device double[9]. */
+ * Each particle's terms and each thread's partial sums (a fixed stride of
+ * particles) are formed in double-float arithmetic on the float32 pipe
+ * (exact products by fma, TwoSum accumulation, about 48 significant bits;
+ * |a| by a float32 root plus one Newton correction), and the per-thread sums
+ * are reduced in float64.  v (vx, vy, vz), a (ax, ay, az) and phi may each be
+ * NULL (their sums are then 0); v and a are all three components or none.
+ * out: device double[9]. */
 int hacc_moments(int64_t N, const float *m, const float *vx, const float *vy, const float *vz,
                  const float *ax, const float *ay, const float *az, const float *phi, double *out,
                  void *ws, size_t ws_bytes, void *stream);

@@ -49,7 +49,7 @@ k_kick(int64_t N, float *__restrict__ vx, float *__restrict__ vy, float *__restr
 }
 
 constexpr int MOM_THREADS = 256;
-constexpr int MOM_BLOCKS = 1024;
+constexpr int MOM_BLOCKS = 4096;  // 1M threads: enough loads in flight for a bandwidth-bound pass
 constexpr int MOM_N = 9;  // sums: m v (3), m a (3), kinetic, m |a|, potential
 
 __device__ __forceinline__ double block_sum(double v, double *sh)
@@ -66,32 +66,126 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return r;
 }
 
+// Double-float arithmetic on the float32 pipe (an unevaluated sum hi + lo of
+// two float32 values, about 48 significant bits): GB300's float64 pipe is
+// narrow, so the per-particle terms and each thread's partial sums are formed
+// this way and only the per-thread totals are reduced in float64.
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// TwoProduct with one fma: p + e == a * b exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+struct DF {
+    float hi = 0.0f, lo = 0.0f;
+    // += (xh + xl): TwoSum of the leading parts, the trailing parts added to
+    // the error, then renormalised (Dekker's Fast2Sum)
+    __device__ __forceinline__ void add(float xh, float xl)
+    {
+        float s, e;
+        two_sum(hi, xh, s, e);
+        e = __fadd_rn(e, __fadd_rn(lo, xl));
+        hi = __fadd_rn(s, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// (h + l) * b for a double-float h + l and a float32 b
+__device__ __forceinline__ void df_mul(float h, float l, float b, float &ph, float &pl)
+{
+    float e;
+    two_prod(h, b, ph, e);
+    pl = __fmaf_rn(l, b, e);
+}
+
+// x0^2 + x1^2 + x2^2 as a double-float
+__device__ __forceinline__ void df_norm2(float x0, float x1, float x2, float &h, float &l)
+{
+    float p0, e0, p1, e1, p2, e2, s, e;
+    two_prod(x0, x0, p0, e0);
+    two_prod(x1, x1, p1, e1);
+    two_prod(x2, x2, p2, e2);
+    two_sum(p0, p1, s, e);
+    float t, f;
+    two_sum(s, p2, t, f);
+    const float lo = __fadd_rn(__fadd_rn(e, f), __fadd_rn(__fadd_rn(e0, e1), e2));
+    h = __fadd_rn(t, lo);
+    l = __fsub_rn(lo, __fsub_rn(h, t));
+}
+
+// sqrt(h + l) as a double-float: the float32 root and one Newton correction
+// from the exact residual (h - r^2 formed with an fma)
+__device__ __forceinline__ void df_sqrt(float h, float l, float &rh, float &rl)
+{
+    if (!(h > 0.0f)) {
+        rh = sqrtf(h);
+        rl = 0.0f;
+        return;
+    }
+    const float r = sqrtf(h);
+    const float res = __fadd_rn(__fmaf_rn(-r, r, h), l);
+    rh = r;
+    rl = res / __fmul_rn(2.0f, r);
+}
+
 // Fixed grid and fixed per-thread striding: the summation order depends only
-// on N, so the float64 results are reproducible run to run.
+// on N, so the float64 results are reproducible run to run.  Per particle and
+// per thread in double-float (above), across threads and blocks in float64.
 __global__ void __launch_bounds__(MOM_THREADS)
 k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restrict__ vx, const float *__restrict__ vy,
                   const float *__restrict__ vz, const float *__restrict__ ax, const float *__restrict__ ay,
                   const float *__restrict__ az, const float *__restrict__ phi, double *__restrict__ part)
 {
     __shared__ double sh[MOM_THREADS / 32];
-    double s[MOM_N] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    DF s[MOM_N];
+#pragma unroll 4
     for (int64_t i = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x; i < N; i += (int64_t)MOM_BLOCKS * MOM_THREADS) {
-        const double mi = m[i];
-        const double v0 = vx ? vx[i] : 0.0, v1 = vy ? vy[i] : 0.0, v2 = vz ? vz[i] : 0.0;
-        const double a0 = ax ? ax[i] : 0.0, a1 = ay ? ay[i] : 0.0, a2 = az ? az[i] : 0.0;
-        s[0] += mi * v0;
-        s[1] += mi * v1;
-        s[2] += mi * v2;
-        s[3] += mi * a0;
-        s[4] += mi * a1;
-        s[5] += mi * a2;
-        s[6] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
-        s[7] += mi * sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-        s[8] += phi ? 0.5 * mi * (double)phi[i] : 0.0;
+        const float mi = m[i];
+        float p, e, h, l;
+        if (vx) {
+            const float v0 = vx[i], v1 = vy[i], v2 = vz[i];
+            two_prod(mi, v0, p, e);
+            s[0].add(p, e);
+            two_prod(mi, v1, p, e);
+            s[1].add(p, e);
+            two_prod(mi, v2, p, e);
+            s[2].add(p, e);
+            df_norm2(v0, v1, v2, h, l);
+            df_mul(h, l, mi, p, e);
+            s[6].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));  // halving is exact
+        }
+        if (ax) {
+            const float a0 = ax[i], a1 = ay[i], a2 = az[i];
+            two_prod(mi, a0, p, e);
+            s[3].add(p, e);
+            two_prod(mi, a1, p, e);
+            s[4].add(p, e);
+            two_prod(mi, a2, p, e);
+            s[5].add(p, e);
+            float rh, rl;
+            df_norm2(a0, a1, a2, h, l);
+            df_sqrt(h, l, rh, rl);
+            df_mul(rh, rl, mi, p, e);
+            s[7].add(p, e);
+        }
+        if (phi) {
+            two_prod(mi, phi[i], p, e);
+            s[8].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));
+        }
     }
 #pragma unroll
     for (int k = 0; k < MOM_N; ++k) {
-        double r = block_sum(s[k], sh);
+        double r = block_sum(s[k].value(), sh);
         if (threadIdx.x == 0) part[(int64_t)k * MOM_BLOCKS + blockIdx.x] = r;
     }
 }
@@ -183,6 +277,8 @@ extern "C" int hacc_moments(int64_t N, const float *m, const float *vx, const fl
 {
     if (N < 0 || !out || !ws) return HACC_ERR_INVALID;
     if (N > 0 && !m) return HACC_ERR_INVALID;
+    if ((vx || vy || vz) && !(vx && vy && vz)) return HACC_ERR_INVALID;
+    if ((ax || ay || az) && !(ax && ay && az)) return HACC_ERR_INVALID;
     if (ws_bytes < hacc_moments_workspace_size(N)) return HACC_ERR_CAPACITY;
     cudaStream_t st = as_stream(stream);
     k_moments_partial<<<MOM_BLOCKS, MOM_THREADS, 0, st>>>(N, m, vx, vy, vz, ax, ay, az, phi,

@@ -377,3 +377,30 @@ def test_kick_drift_against_oracle(torch, hs):
     assert np.allclose(xt3.cpu().numpy().T, x_ref3, rtol=0, atol=4e-6)
     with pytest.raises(hs.HaccError):  # neither a kick nor a drift
         hs.hacc_kick(None, N, v2[0], v2[1], v2[2], None, None, None, 0.0)
+
+
+def test_moments_double_float_against_float64(torch, hs):
+    """hacc_moments forms its terms and per-thread sums in double-float on the
+    float32 pipe: on inputs spanning six decades, of both signs, with sums that
+    cancel, every moment matches the float64 sum of the same float32 inputs to
+    1e-12 of the sum of the terms' magnitudes."""
+    N = 1_000_003
+    rng = np.random.default_rng(41)
+    scale = lambda: 10.0 ** rng.uniform(-3, 3, N)
+    m = rng.uniform(0.5, 2.0, N).astype(np.float32)
+    v = (rng.normal(size=(3, N)) * scale()).astype(np.float32)
+    a = (rng.normal(size=(3, N)) * scale()).astype(np.float32)
+    a[:, N // 2:] = -a[:, :N - N // 2]  # the second half cancels the first (up to one column)
+    phi = (rng.normal(size=N) * scale()).astype(np.float32)
+    L = np.array([64.0], np.float32)
+    sr = hs.ShortRange(L, np.array([0, N], np.int64), RC)
+    dev = lambda x: torch.tensor(x, device="cuda")
+    got = sr.moments(dev(m), dev(v), dev(a), dev(phi)).cpu().numpy()
+    m64, v64, a64, p64 = (x.astype(np.float64) for x in (m, v, a, phi))
+    terms = [m64 * v64[0], m64 * v64[1], m64 * v64[2], m64 * a64[0], m64 * a64[1], m64 * a64[2],
+             0.5 * m64 * (v64 ** 2).sum(0), m64 * np.sqrt((a64 ** 2).sum(0)), 0.5 * m64 * p64]
+    for k, t in enumerate(terms):
+        assert abs(got[k] - t.sum()) <= 1e-12 * np.abs(t).sum(), (k, got[k], t.sum())
+    # the same sums with v or a left out, and the order-fixed result repeats bit for bit
+    got2 = sr.moments(dev(m), None, dev(a), None).cpu().numpy()
+    assert np.all(got2[[0, 1, 2, 6, 8]] == 0.0) and np.array_equal(got2[[3, 4, 5, 7]], got[[3, 4, 5, 7]])

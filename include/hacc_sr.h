@@ -195,7 +195,7 @@ int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float 
  * (inside a captured stream, a host callback, a real-time loop).  The scratch
  * space that hacc_bin takes as `ws` is instead one fixed array that the
  * library places in device memory when it is loaded: HACC_BIN_NOALLOC_BYTES
- * (9 MiB), enough for up to 262,144 particles in up to 65,536 cells; every
+ * (9 MiB), enough for up to 262,144 particles (in any number of cells); every
  * device that loads the library keeps it until the process exits.  Larger
  * problems return HACC_ERR_CAPACITY (use hacc_bin with a workspace).  The
  * caller still passes the inputs and the outputs in `out`; nothing is

@@ -67,15 +67,15 @@ __device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, con
     return c;
 }
 
-// Pass 1: per particle, its cell key, its (offset, mass) record in input
-// order, and the cell histogram; with mass_varies, whether any mass differs
-// from the first particle's (N > 0).
+// Pass 1: per particle, its cell key and its (offset, mass) record in input
+// order; with mass_varies, whether any mass differs from the first
+// particle's (N > 0).
 __global__ void __launch_bounds__(KEY_THREADS)
 k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *__restrict__ x,
            const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dx,
            const float *__restrict__ dy, const float *__restrict__ dz, const float *__restrict__ m,
            int32_t *__restrict__ cell_of, int32_t *__restrict__ keys, float4 *__restrict__ rec,
-           int32_t *__restrict__ counts, uint32_t *status, uint32_t *mass_varies)
+           uint32_t *status, uint32_t *mass_varies)
 {
     MassCheck mc(m, mass_varies);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -93,12 +93,25 @@ k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *
         r.w = m[i];
         rec[i] = r;
         mc.check(r.w);
-        // one atomic per distinct cell of the warp: consecutive particles of a halo share cells
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, key);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
     }
     mc.finish();
+}
+
+// cell_start from the sorted keys: the first slot whose key is >= c (a binary
+// search per cell c in [0, n_cells]; cell n_cells gets N), empty cells
+// included.
+__global__ void __launch_bounds__(256)
+k_cell_starts(const int32_t *__restrict__ skeys, int64_t N, int64_t n_cells, int32_t *__restrict__ cell_start)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)skeys[mid] < c) lo = mid + 1; else hi = mid;
+        }
+        cell_start[c] = (int32_t)lo;
+    }
 }
 
 // Radix pass, step 1: digit histogram of each 4096-key tile, digit-major.
@@ -120,16 +133,27 @@ k_radix_hist(const int32_t *__restrict__ keys, int64_t N, int shift, int nblk, i
 
 // Radix pass, step 2: stable scatter.  Warp w owns tile positions
 // [512 w, 512 w + 512), item k of lane l is position 512 w + 32 k + l, so
-// (warp, item, lane) order is input order; equal digits keep that order.
+// (warp, item, lane) order is input order; equal digits keep that order.  The
+// tile is first sorted by digit in shared memory, so that the stores to global
+// memory run along each digit's consecutive destinations (one transaction per
+// run instead of one per element); the destinations themselves are those of
+// a direct scatter.
 __global__ void __launch_bounds__(R_THREADS)
 k_radix_scatter(const int32_t *__restrict__ keys_in, const int32_t *__restrict__ vals_in, int64_t N,
                 int shift, int nblk, const int32_t *__restrict__ offs, int32_t *__restrict__ keys_out,
                 int32_t *__restrict__ vals_out)
 {
-    __shared__ int32_t wcnt[R_WARPS][RADIX + 1];
+    // per-warp digit counts, then (reused) the tile's keys and values in digit order
+    __shared__ union {
+        int32_t wcnt[R_WARPS][RADIX + 1];
+        int32_t stage[2][R_TILE];
+    } sm;
+    static_assert(sizeof(sm.stage) <= sizeof(sm.wcnt), "staging fits the count array");
     __shared__ int32_t base_d[RADIX];
+    __shared__ int32_t tstart[RADIX];  // first tile-local slot of each digit
+    __shared__ int32_t wsum[R_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < R_WARPS * (RADIX + 1); t += R_THREADS) (&wcnt[0][0])[t] = 0;
+    for (int t = threadIdx.x; t < R_WARPS * (RADIX + 1); t += R_THREADS) (&sm.wcnt[0][0])[t] = 0;
     for (int d = threadIdx.x; d < RADIX; d += R_THREADS) base_d[d] = offs[(int64_t)d * nblk + blockIdx.x];
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -142,32 +166,84 @@ k_radix_scatter(const int32_t *__restrict__ keys_in, const int32_t *__restrict__
         key[k] = valid ? keys_in[i] : 0;
         int d = valid ? (int)(((uint32_t)key[k] >> shift) & (RADIX - 1)) : RADIX;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
-        int cur = wcnt[warp][d];
+        int cur = sm.wcnt[warp][d];
         __syncwarp();
-        if (lane == __ffs(peers) - 1) wcnt[warp][d] = cur + __popc(peers);
+        if (lane == __ffs(peers) - 1) sm.wcnt[warp][d] = cur + __popc(peers);
         __syncwarp();
         rank[k] = cur + __popc(peers & lt_mask);
     }
     __syncthreads();
+    // per digit: prefix over warps, and the tile's count
     for (int d = threadIdx.x; d < RADIX; d += R_THREADS) {
         int run = 0;
 #pragma unroll
         for (int w = 0; w < R_WARPS; ++w) {
-            int c = wcnt[w][d];
-            wcnt[w][d] = run;
+            int c = sm.wcnt[w][d];
+            sm.wcnt[w][d] = run;
             run += c;
+        }
+        tstart[d] = run;
+    }
+    __syncthreads();
+    // exclusive scan of the tile's digit counts (four consecutive digits per thread)
+    {
+        constexpr int PER = RADIX / R_THREADS;
+        static_assert(PER * R_THREADS == RADIX, "digits per thread");
+        int v[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            v[q] = tstart[threadIdx.x * PER + q];
+            sum += v[q];
+        }
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        int run = before + inc - sum;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            tstart[threadIdx.x * PER + q] = run;
+            run += v[q];
         }
     }
     __syncthreads();
+    // tile-local slots and values, before the count array is reused
+    int32_t lp[R_ITEMS], val[R_ITEMS];
 #pragma unroll
     for (int k = 0; k < R_ITEMS; ++k) {
         int64_t i = p0 + 32 * k;
         if (i < N) {
             int d = (int)(((uint32_t)key[k] >> shift) & (RADIX - 1));
-            int64_t pos = (int64_t)base_d[d] + wcnt[warp][d] + rank[k];
-            keys_out[pos] = key[k];
-            vals_out[pos] = vals_in ? vals_in[i] : (int32_t)i;
+            lp[k] = tstart[d] + sm.wcnt[warp][d] + rank[k];
+            val[k] = vals_in ? vals_in[i] : (int32_t)i;
+        } else {
+            lp[k] = -1;
+            val[k] = 0;
         }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < R_ITEMS; ++k) {
+        if (lp[k] >= 0) {
+            sm.stage[0][lp[k]] = key[k];
+            sm.stage[1][lp[k]] = val[k];
+        }
+    }
+    __syncthreads();
+    const int64_t tile0 = (int64_t)blockIdx.x * R_TILE;
+    const int nv = (int)(N - tile0 < R_TILE ? N - tile0 : R_TILE);
+    for (int j = threadIdx.x; j < nv; j += R_THREADS) {
+        const int32_t kk = sm.stage[0][j];
+        const int d = (int)(((uint32_t)kk >> shift) & (RADIX - 1));
+        const int64_t pos = (int64_t)base_d[d] + (j - tstart[d]);
+        keys_out[pos] = kk;
+        vals_out[pos] = sm.stage[1][j];
     }
 }
 
@@ -182,9 +258,9 @@ k_bin_gather(int64_t N, const int32_t *__restrict__ perm, const float4 *__restri
 }
 
 struct BinWs {
-    int32_t *keys, *counts;
+    int32_t *keys;
     float4 *rec;
-    char *scan_ws, *sort_ws;
+    char *sort_ws;
     size_t total;
 };
 
@@ -203,8 +279,6 @@ BinWs bin_ws_layout(const hacc_mesh *mesh, void *ws)
     };
     b.rec = reinterpret_cast<float4 *>(take((size_t)N * sizeof(float4)));
     b.keys = reinterpret_cast<int32_t *>(take((size_t)N * 4));
-    b.counts = reinterpret_cast<int32_t *>(take((size_t)mesh->n_cells * 4));
-    b.scan_ws = take(scan_workspace_bytes(mesh->n_cells));
     b.sort_ws = take(sort_workspace_bytes(N));
     b.total = off;
     return b;
@@ -219,8 +293,10 @@ size_t sort_workspace_bytes(int64_t N)
            round_up((size_t)(nhist + 1) * 4, 256) + scan_workspace_bytes(nhist);
 }
 
-int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st)
+int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st,
+                      const int32_t **sorted_keys)
 {
+    if (sorted_keys) *sorted_keys = keys;
     if (N <= 0) return HACC_OK;
     char *p = reinterpret_cast<char *>(ws);
     const int nblk = radix_blocks(N);
@@ -254,6 +330,7 @@ int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, 
         kin = kout;
         vin = vout;
     }
+    if (sorted_keys) *sorted_keys = kin;
     return HACC_OK;
 }
 
@@ -293,24 +370,25 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     if (ws_bytes < b.total) return HACC_ERR_CAPACITY;
     cudaStream_t st = as_stream(stream);
 
-    HACC_CUDA_TRY(cudaMemsetAsync(b.counts, 0, (size_t)mesh->n_cells * 4, st));
     if (out->mass_varies) HACC_CUDA_TRY(cudaMemsetAsync(out->mass_varies, 0, sizeof(uint32_t), st));
-    if (N > 0) {
-        k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(
-            mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m, out->cell_of, b.keys, b.rec, b.counts, status,
-            out->mass_varies);
-        HACC_LAUNCH_CHECK();
+    if (N == 0) {
+        HACC_CUDA_TRY(cudaMemsetAsync(out->cell_start, 0, (size_t)(mesh->n_cells + 1) * 4, st));
+        return HACC_OK;
     }
-    int rc = scan_exclusive_i32(b.counts, out->cell_start, mesh->n_cells, b.scan_ws, st);
-    if (rc) return rc;
-    if (N == 0) return HACC_OK;
+    k_bin_keys<<<grid_for(N, KEY_THREADS), KEY_THREADS, 0, st>>>(mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m,
+                                                                 out->cell_of, b.keys, b.rec, status,
+                                                                 out->mass_varies);
+    HACC_LAUNCH_CHECK();
 
-    // stable sort of the particle indices by cell: perm
+    // stable sort of the particle indices by cell: perm, and the sorted keys for cell_start
     const uint32_t maxkey = (uint32_t)(mesh->n_cells - 1);
     int bits = 0;
     while (bits < 32 && (maxkey >> bits) != 0) ++bits;
-    rc = sort_index_stable(b.keys, N, bits, out->perm, b.sort_ws, st);
+    const int32_t *skeys = nullptr;
+    int rc = sort_index_stable(b.keys, N, bits, out->perm, b.sort_ws, st, &skeys);
     if (rc) return rc;
+    k_cell_starts<<<grid_for(mesh->n_cells + 1, 256), 256, 0, st>>>(skeys, N, mesh->n_cells, out->cell_start);
+    HACC_LAUNCH_CHECK();
     k_bin_gather<<<grid_for(N, 256), 256, 0, st>>>(N, out->perm, b.rec,
                                                    reinterpret_cast<float4 *>(out->sorted4));
     HACC_LAUNCH_CHECK();

@@ -121,8 +121,10 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, cud
 
 // Stable sort of indices by int32 key (LSD radix, 10-bit digits, only the low
 // `bits` bits significant): order[k] = index of the k-th smallest key, ties
-// in index order.  ws: sort_workspace_bytes(N).  Deterministic.
+// in index order.  ws: sort_workspace_bytes(N).  Deterministic.  If
+// sorted_keys is given it receives the keys in sorted order (inside ws).
 size_t sort_workspace_bytes(int64_t N);
-int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st);
+int sort_index_stable(const int32_t *keys, int64_t N, int bits, int32_t *order, void *ws, cudaStream_t st,
+                      const int32_t **sorted_keys = nullptr);
 
 }  // namespace hacc

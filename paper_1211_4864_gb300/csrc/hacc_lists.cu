@@ -16,15 +16,39 @@ __device__ __forceinline__ void cell_coords(int64_t local, int n, int &cx, int &
     cz = (int)(local / ((int64_t)n * n));
 }
 
+// Stencil mask of one reach: the box-distance predicate depends only on the
+// offset and the volume, so a block evaluates it once per offset (float64 is
+// slow on this GPU) for the volume of its first cell; a cell of another
+// volume, or a reach beyond the buffer, evaluates it directly.
+constexpr int STENCIL_MAX = 15 * 15 * 15;  // reach up to 7
+
 __global__ void __launch_bounds__(256)
 k_lists_fill(const hacc_volume *__restrict__ vols, int V, int64_t n_cells, int64_t n_entries,
              int64_t *__restrict__ nbr_off, int32_t *__restrict__ nbr_cell, int8_t *__restrict__ nbr_shift,
              uint32_t *status)
 {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    __shared__ unsigned char mask[STENCIL_MAX];
+    __shared__ int mask_vol;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_cells; base += G) {
+        // the block's mask for the volume of its first cell this round
+        __syncthreads();
+        const int vb = find_volume_by_cell(vols, V, base);
+        {
+            const hacc_volume &vol = vols[vb];
+            const int R = vol.R, D = 2 * R + 1;
+            const double w = (double)vol.w, rc = (double)vol.rcut;
+            if (D * D * D <= STENCIL_MAX)
+                for (int o = threadIdx.x; o < D * D * D; o += blockDim.x)
+                    mask[o] = cells_within(o % D - R, (o / D) % D - R, o / (D * D) - R, w, rc) ? 1 : 0;
+            if (threadIdx.x == 0) mask_vol = D * D * D <= STENCIL_MAX ? vb : -1;
+        }
+        __syncthreads();
+        const int64_t c = base + threadIdx.x;
+        if (c >= n_cells) continue;
         int v = find_volume_by_cell(vols, V, c);
         const hacc_volume &vol = vols[v];
+        const bool use_mask = v == mask_vol;
         int n = vol.n, R = vol.R;
         int64_t local = c - vol.cell_base;
         int cx, cy, cz;
@@ -33,10 +57,11 @@ k_lists_fill(const hacc_volume *__restrict__ vols, int V, int64_t n_cells, int64
         const int64_t e_end = e + vol.S;  // never write past this cell's planned slots
         nbr_off[c] = e;
         double w = (double)vol.w, rc = (double)vol.rcut;
+        int o = 0;
         for (int dz = -R; dz <= R; ++dz)
             for (int dy = -R; dy <= R; ++dy)
-                for (int dx = -R; dx <= R; ++dx) {
-                    if (!cells_within(dx, dy, dz, w, rc)) continue;
+                for (int dx = -R; dx <= R; ++dx, ++o) {
+                    if (use_mask ? !mask[o] : !cells_within(dx, dy, dz, w, rc)) continue;
                     int px = cx + dx, py = cy + dy, pz = cz + dz;
                     int sx = 0, sy = 0, sz = 0;
                     if (px < 0) { px += n; sx = -1; } else if (px >= n) { px -= n; sx = 1; }

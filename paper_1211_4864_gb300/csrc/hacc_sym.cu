@@ -188,15 +188,48 @@ struct AccI {
     }
 };
 
-// The chunk against itself, block B: its i set B held as j.  Set B meets it
-// above the diagonal (j > i), sets below B meet all of it, sets above none.
+// The chunk against itself, block B: its i set B held as j.  Sets below B
+// meet all of it (32 steps); set B meets its own records only at steps 1..15,
+// and at step 16 on the low half-warp: the pair of lanes a and b comes round
+// at step (b - a) mod 32 in lane a and at the complementary step in lane b,
+// so this meets each pair of the set once, in 16 of the 32 steps.  Block 0
+// (no set below it) stops after 17 steps and flushes each j from the lane it
+// has reached.
 template <int IPL, int B, bool EQ>
-__device__ __forceinline__ void diag_block(const float4 (&oi)[IPL], const bool (&active)[IPL], int ib,
-                                           const PairConsts &K, AccI<IPL> &A, double *acc, int64_t N, int lane)
+__device__ __forceinline__ void diag_block(const float4 (&oi)[IPL], int ib, int ie, const PairConsts &K,
+                                           AccI<IPL> &A, double *acc, int64_t N, int lane)
 {
-    constexpr unsigned SKIP = ((1u << IPL) - 1u) & ~((2u << B) - 1u);
-    JRec J{oi[B].x, oi[B].y, oi[B].z, oi[B].w, 0.f, 0.f, 0.f, active[B] ? ib + 32 * B + lane : -1};
-    rotate_block<IPL, (1u << B), SKIP, EQ>(J, oi, K, A.a, lane);
+    constexpr unsigned BELOW = (1u << B) - 1u;
+    const int src = (lane + 1) & 31;
+    const int i_own = ib + 32 * B + lane;
+    JRec J{oi[B].x, oi[B].y, oi[B].z, oi[B].w, 0.f, 0.f, 0.f, i_own < ie ? i_own : -1};
+    auto below = [&]() {
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if ((BELOW >> u) & 1u) pair_sym<false, EQ>(J, oi[u], K, A.a[u], true);
+    };
+    below();  // step 0: the set's own records meet themselves (d = 0): nothing
+    rotate_one<EQ>(J, src);
+#pragma unroll 4
+    for (int k = 1; k <= 16; ++k) {
+        below();
+        pair_sym<true, EQ>(J, oi[B], K, A.a[B], (k < 16) | (lane < 16));
+        rotate_one<EQ>(J, src);
+    }
+    if constexpr (B > 0) {
+#pragma unroll 3
+        for (int k = 17; k < 32; ++k) {
+            below();
+            rotate_one<EQ>(J, src);
+        }
+    } else {
+        const int h = (lane + 17) & 31;  // the record this lane holds after 17 steps
+        const int i_h = ib + 32 * B + h;
+        J.slot = i_h < ie ? i_h : -1;
+        // equal masses do not rotate: the lane's own may be an empty lane's 0, so take the
+        // common mass from lane 0 (always a particle of the task)
+        if constexpr (EQ) J.m = __shfl_sync(FULL, J.m, 0);
+    }
     flush_j<EQ>(J, acc, N);
 }
 
@@ -245,12 +278,12 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
     if constexpr (HALF) {
         diag_block_half<EQ>(oi, active[0], ib, K, A, acc, N, lane);
     } else {
-        diag_block<IPL, 0, EQ>(oi, active, ib, K, A, acc, N, lane);
+        diag_block<IPL, 0, EQ>(oi, ib, ie, K, A, acc, N, lane);
     }
-    if constexpr (IPL > 1) diag_block<IPL, 1, EQ>(oi, active, ib, K, A, acc, N, lane);
+    if constexpr (IPL > 1) diag_block<IPL, 1, EQ>(oi, ib, ie, K, A, acc, N, lane);
     if constexpr (IPL > 2) {
-        diag_block<IPL, 2, EQ>(oi, active, ib, K, A, acc, N, lane);
-        diag_block<IPL, 3, EQ>(oi, active, ib, K, A, acc, N, lane);
+        diag_block<IPL, 2, EQ>(oi, ib, ie, K, A, acc, N, lane);
+        diag_block<IPL, 3, EQ>(oi, ib, ie, K, A, acc, N, lane);
     }
     A.fold();
 

@@ -45,9 +45,9 @@ FORCE_TRAFFIC = {
     "gather": {"workload": "clustered256", "bytes": 2221459456 + 966782208,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
                "sha256": "40962c6002c7f1679c570ca48baf21394977c86d52b4064efecc1ff3f93eaf95"},
-    "symmetric": {"workload": "clustered256", "bytes": 2793387264 + 1488423680,
+    "symmetric": {"workload": "clustered256", "bytes": 2792153856 + 1488596480,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
-                  "sha256": "fd448cf8dbca355f7bac05b4940cc4358f8d28b63c61d8ba10fff9093c2c9003"},
+                  "sha256": "f01f4b20d713de8eb4923588f1d6f2fe1469ebe8be937a54fcef206b87bb883a"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

@@ -140,6 +140,19 @@ def test_bin_lists_bit_exact_fine_mesh_and_edge_positions(torch, hs):
     check_bin_lists(torch, hs, w, 1.6, 3.0, split_T=7)
 
 
+def test_bin_lists_bit_exact_reach8(torch, hs):
+    """Cells of 0.4 grid units against r_c = 3 (reach 8: a 17^3 stencil, more
+    offsets than the list kernel's per-block predicate table holds, so every
+    offset is decided directly; the other list tests run on the table), in two
+    volumes of 17 and 18 cells per side."""
+    wa = uniform_box(400, 7.0, seed=43)
+    wb = uniform_box(500, 7.5, seed=44)
+    cat = lambda f: np.concatenate([getattr(wa, f), getattr(wb, f)])
+    w = Workload("reach8", cat("x"), cat("y"), cat("z"), cat("m"), cat("vx"), cat("vy"), cat("vz"),
+                 np.array([7.0, 7.5], np.float32), np.array([0, 400, 900], np.int64))
+    check_bin_lists(torch, hs, w, 0.4, 3.0, split_T=16)
+
+
 def test_bin_lists_bit_exact_batched_volumes(torch, hs):
     w = batched_volumes(12, n_lo=800, n_hi=6000, seed=8)
     check_bin_lists(torch, hs, w, 3.0, 3.0, split_T=32)

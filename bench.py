@@ -47,7 +47,7 @@ FORCE_TRAFFIC = {
                "sha256": "40962c6002c7f1679c570ca48baf21394977c86d52b4064efecc1ff3f93eaf95"},
     "symmetric": {"workload": "clustered256", "bytes": 2792153856 + 1488596480,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
-                  "sha256": "f01f4b20d713de8eb4923588f1d6f2fe1469ebe8be937a54fcef206b87bb883a"},
+                  "sha256": "7b5c9fe81dfb3efe0942d83116bd638af25458d80dd8e5524ba5e7689f7785b2"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

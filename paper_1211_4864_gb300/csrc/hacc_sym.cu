@@ -54,8 +54,8 @@ __device__ __forceinline__ void rotate_one(JRec &J, int src)
 }
 
 // One pair, both sides: a_i += m_j f d, f_j -= m_i f d (equal masses: both
-// += f d), predicated on the cutoff (and on `ok`, the upper-triangle test of a
-// diagonal block).
+// += f d), predicated on the cutoff (and on `ok`, a diagonal block's test that
+// meets each pair of a set once).
 template <bool MASKED, bool EQ>
 __device__ __forceinline__ void pair_sym(JRec &J, const float4 &oi, const PairConsts &K, float (&ai)[3], bool ok)
 {

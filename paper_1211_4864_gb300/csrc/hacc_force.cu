@@ -230,8 +230,6 @@ __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, cons
 
 
 
-// One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
-// entry of the cell's neighbour list.  Returns false if a wait ran out.
 template <int MODE, int IPL>
 __device__ __forceinline__ auto make_acc(float *comp, int lane)
 {
@@ -241,10 +239,18 @@ __device__ __forceinline__ auto make_acc(float *comp, int lane)
         return AccAdj<MODE, IPL>(comp, lane);
 }
 
+// One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
+// entry of the cell's neighbour list.  Returns false if a wait ran out.
+// With one i per lane and at most 16 i (half, decided per task), lanes l and
+// l + 16 hold the same i and each takes half of every staged piece of j
+// records; the two compensated partial sums are added in a fixed order at the
+// end, so the result stays deterministic.
 template <int MODE, int JT, int STAGES, int IPL, bool EQ>
 __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> &ring, float *comp, int lane,
                                          int c, int ib, int ie, const hacc_volume &vol)
 {
+    const bool half = IPL == 1 && ie - ib <= 16;
+    const int il = half ? (lane & 15) : lane;  // this lane's i within the task
     const PairConsts &K = a.k;
     const int n = vol.n;
     const float w = vol.w;
@@ -257,7 +263,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
     bool active[IPL];
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        const int i = ib + lane + 32 * u;
+        const int i = ib + il + 32 * u;
         active[u] = i < ie;
         oi[u] = active[u] ? a.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -266,7 +272,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
     for (int u = 0; u < IPL; ++u) {
         li[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (is_adjoint(MODE)) {
-            if (active[u]) li[u] = a.lam[ib + lane + 32 * u];
+            if (active[u]) li[u] = a.lam[ib + il + 32 * u];
         }
     }
     auto A = make_acc<MODE, IPL>(comp, lane);
@@ -328,12 +334,25 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
                         op[u][2] = oi[u].z - dz;
                     }
                 }
-                if constexpr (MODE == FORCE)
-                    tile_force<IPL, EQ>(tj + filled, n, op, K, A);
-                else if constexpr (MODE == POTENTIAL)
-                    tile_potential<IPL>(tj + filled, n, op, K, A);
-                else
-                    tile_adjoint<MODE, IPL, EQ>(tj + filled, tj + JT + filled, n, op, oi, li, K, A);
+                // the pair loop over records [o, o + m) of the staged tile
+                auto tile = [&](int o, int m) {
+                    if constexpr (MODE == FORCE)
+                        tile_force<IPL, EQ>(tj + o, m, op, K, A);
+                    else if constexpr (MODE == POTENTIAL)
+                        tile_potential<IPL>(tj + o, m, op, K, A);
+                    else
+                        tile_adjoint<MODE, IPL, EQ>(tj + o, tj + JT + o, m, op, oi, li, K, A);
+                };
+                if constexpr (IPL == 1) {
+                    // half: lanes < 16 take records [0, n/2) and, for odd n, record
+                    // n/2 alone; lanes >= 16 the rest.  Equal trip counts keep the
+                    // loop converged.
+                    const int hn = n >> 1;
+                    tile(filled + (half && (lane & 16) ? hn + (n & 1) : 0), half ? hn : n);
+                    if (half && (n & 1) && lane < 16) tile(filled + hn, 1);
+                } else {
+                    tile(filled, n);
+                }
                 filled += n;
                 coff += n;
             }
@@ -343,10 +362,30 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             ring.produce(a, lane, ng, cnt, jb, pk, poff);
         }
     }
+    if (half) {
+        // lane l (< 16) adds lane l + 16's compensated sums to its own
+        if constexpr (MODE == FORCE || MODE == POTENTIAL) {
+#pragma unroll
+            for (int k = 0; k < (MODE == FORCE ? 3 : 1); ++k) {
+                const float h2 = __shfl_down_sync(FULL, A.h[0][k], 16), l2 = __shfl_down_sync(FULL, A.l[0][k], 16);
+                two_sum_acc(A.h[0][k], A.l[0][k], h2);
+                A.l[0][k] = __fadd_rn(A.l[0][k], l2);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < decltype(A)::NACC; ++k) {
+                float h = A.hi(0, k), l = A.lo(0, k);
+                const float h2 = __shfl_down_sync(FULL, h, 16), l2 = __shfl_down_sync(FULL, l, 16);
+                two_sum_acc(h, l, h2);
+                A.hi(0, k) = h;
+                A.lo(0, k) = __fadd_rn(l, l2);
+            }
+        }
+    }
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        if (!active[u]) continue;
-        const int o = a.perm[ib + lane + 32 * u];
+        if (!active[u] || (half && lane >= 16)) continue;
+        const int o = a.perm[ib + il + 32 * u];
         if constexpr (MODE == FORCE && EQ) {
             a.out_x[o] = oi[u].w * (A.h[u][0] + A.l[u][0]);
             a.out_y[o] = oi[u].w * (A.h[u][1] + A.l[u][1]);
@@ -379,7 +418,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
 
 // Persistent work-stealing kernel: each warp takes tasks from a global
 // counter until none is left.  A task of more than 32 particles runs two i
-// particles per lane.
+// particles per lane, one of at most 16 runs each i on two lanes.
 // Register budgets: the forward and potential kernels keep 80 registers so that
 // 3 CTAs (24 warps) fit an SM; the adjoint's staging needs twice the shared
 // memory, which caps it at 2 CTAs, so it may use up to 128 registers.

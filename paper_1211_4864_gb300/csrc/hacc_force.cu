@@ -152,7 +152,10 @@ __device__ __forceinline__ void tile_potential(const float4 *__restrict__ tj, in
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
 // Equal masses (EQ): V += f and X += fp2 (d.(lam_j - lam_i)) d, so that
 // dL/dx_i = m (U - lam_i V + X); one dot product instead of two without G.
-// One pair of the adjoint, accumulated into acc[8] = (U, V, X, G) of one i.
+// Equal masses without G (the W form): the three sums fold into one,
+// W += f (lam_j - lam_i) + fp2 (d.(lam_j - lam_i)) d, and dL/dx_i = m W.
+// One pair of the adjoint, accumulated into acc[8] = (U, V, X, G) of one i
+// (the W form: acc[3] = W).
 template <bool GM, bool EQ>
 __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, float oxp, float oyp, float ozp,
                                              float mi, float lix, float liy, float liz, const PairConsts &K,
@@ -168,11 +171,19 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
     float f = t3 + q;
     float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
     float fp2 = fmaf(-3.0f, t3 * t2, qp);
+    if constexpr (EQ && !GM) {
+        const float ex = l.x - lix, ey = l.y - liy, ez = l.z - liz;
+        const float r = fp2 * fmaf(dz, ez, fmaf(dy, ey, dx * ex));
+        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %3, %4;\n\t"
+            "@p fma.rn.f32 %0, %5, %6, %0;\n\t@p fma.rn.f32 %1, %5, %7, %1;\n\t@p fma.rn.f32 %2, %5, %8, %2;\n\t"
+            "@p fma.rn.f32 %0, %9, %10, %0;\n\t@p fma.rn.f32 %1, %9, %11, %1;\n\t@p fma.rn.f32 %2, %9, %12, %2;\n\t}"
+            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2])
+            : "f"(se), "f"(K.rc2e), "f"(f), "f"(ex), "f"(ey), "f"(ez), "f"(r), "f"(dx), "f"(dy), "f"(dz));
+        return;
+    }
     float dlj = fmaf(dz, l.z, fmaf(dy, l.y, dx * l.x));
     float r;
-    if constexpr (EQ && !GM) {
-        r = fp2 * fmaf(dz, l.z - liz, fmaf(dy, l.y - liy, dx * (l.x - lix)));
-    } else if constexpr (EQ) {
+    if constexpr (EQ) {
         r = fp2 * (dlj - fmaf(dz, liz, fmaf(dy, liy, dx * lix)));
     } else {
         const float dli = fmaf(dz, liz, fmaf(dy, liy, dx * lix));
@@ -205,7 +216,8 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
 template <int MODE, int IPL, bool EQ>
 __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, const float4 *__restrict__ tl, int n,
                                              const float (&op)[IPL][3], const float4 (&oi)[IPL],
-                                             const float4 (&li)[IPL], const PairConsts &K, AccAdj<MODE, IPL> &A)
+                                             const float4 (&li)[IPL], const PairConsts &K,
+                                             AccAdj<MODE, IPL, adj_nacc(MODE, EQ)> &A)
 {
     constexpr bool GM = MODE == ADJOINT_GM;
     int j = 0;
@@ -230,13 +242,13 @@ __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, cons
 
 
 
-template <int MODE, int IPL>
+template <int MODE, int IPL, bool EQ>
 __device__ __forceinline__ auto make_acc(float *comp, int lane)
 {
     if constexpr (MODE == FORCE || MODE == POTENTIAL)
         return Acc<MODE, IPL>();
     else
-        return AccAdj<MODE, IPL>(comp, lane);
+        return AccAdj<MODE, IPL, adj_nacc(MODE, EQ)>(comp, lane);
 }
 
 // One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
@@ -275,7 +287,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             if (active[u]) li[u] = a.lam[ib + il + 32 * u];
         }
     }
-    auto A = make_acc<MODE, IPL>(comp, lane);
+    auto A = make_acc<MODE, IPL, EQ>(comp, lane);
 
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
     for (int64_t g0 = e0; g0 < e1; g0 += 32) {
@@ -398,6 +410,11 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             // the sum met particle i itself once (d = 0, se = eps exactly): take that term out
             const float self = pair_potential_of(K.eps, K);
             a.out_x[o] = (A.h[u][0] + A.l[u][0]) - oi[u].w * self;
+        } else if constexpr (adj_wform(MODE, EQ)) {
+            // dL/dx_i = m W
+            a.out_x[o] = oi[u].w * A.total(u, 0);
+            a.out_y[o] = oi[u].w * A.total(u, 1);
+            a.out_z[o] = oi[u].w * A.total(u, 2);
         } else {
             // dL/dx_i = m_i U - lam_i V + X (equal masses: m (U - lam_i V + X)) ;  dL/dm_i = -G
             const float Vs = A.total(u, 3);

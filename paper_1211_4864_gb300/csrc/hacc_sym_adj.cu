@@ -17,6 +17,10 @@ namespace {
 // d_k = x_p - x_k, so that dL/dx_k = m_k U - lam_k V + X and dL/dm_k = -G.
 // For the pair seen from j every term flips sign or swaps: U_j += f lam_i,
 // V_j += m_i f, X_j -= r d, G_j -= f d.lam_i.
+// Equal masses without dL/dm (the W form): the pair's whole term
+// w = f (lam_j - lam_i) + fp2 (d.(lam_j - lam_i)) d is antisymmetric, like a
+// force, so i adds w and j subtracts it; each side carries three sums (u0,
+// u1, u2) and dL/dx_k = m W_k.
 // ---------------------------------------------------------------------------
 
 // One j of an adjoint rotation block: record shifted into the i frame, its
@@ -30,6 +34,7 @@ struct JAdj {
 template <bool GM, bool EQ>
 __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
 {
+    constexpr bool WF = adj_wform(GM ? ADJOINT_GM : ADJOINT, EQ);
     J.x = __shfl_sync(FULL, J.x, src);
     J.y = __shfl_sync(FULL, J.y, src);
     J.z = __shfl_sync(FULL, J.z, src);
@@ -40,6 +45,7 @@ __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
     J.u0 = __shfl_sync(FULL, J.u0, src);
     J.u1 = __shfl_sync(FULL, J.u1, src);
     J.u2 = __shfl_sync(FULL, J.u2, src);
+    if constexpr (WF) return;
     J.v = __shfl_sync(FULL, J.v, src);
     J.x0 = __shfl_sync(FULL, J.x0, src);
     J.x1 = __shfl_sync(FULL, J.x1, src);
@@ -64,14 +70,24 @@ __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const fl
                          K.nc[0]);
     const float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
     const float fp2 = fmaf(-3.0f, t3 * t2, qp);
-    const float dlj = fmaf(dz, J.lz, fmaf(dy, J.ly, dx * J.lx));
-    const float dli = fmaf(dz, li.z, fmaf(dy, li.y, dx * li.x));
     const bool in = ok & (se < K.rc2e);
     const float f = in ? t3 + q : 0.0f;
+    if constexpr (EQ && !GM) {  // the W form
+        const float ex = J.lx - li.x, ey = J.ly - li.y, ez = J.lz - li.z;
+        const float r = in ? fp2 * fmaf(dz, ez, fmaf(dy, ey, dx * ex)) : 0.0f;
+        const float wx = fmaf(f, ex, r * dx), wy = fmaf(f, ey, r * dy), wz = fmaf(f, ez, r * dz);
+        acc[0] += wx;
+        acc[1] += wy;
+        acc[2] += wz;
+        J.u0 -= wx;
+        J.u1 -= wy;
+        J.u2 -= wz;
+        return;
+    }
+    const float dlj = fmaf(dz, J.lz, fmaf(dy, J.ly, dx * J.lx));
+    const float dli = fmaf(dz, li.z, fmaf(dy, li.y, dx * li.x));
     float rr;
-    if constexpr (EQ && !GM)
-        rr = fp2 * fmaf(dz, J.lz - li.z, fmaf(dy, J.ly - li.y, dx * (J.lx - li.x)));
-    else if constexpr (EQ)
+    if constexpr (EQ)
         rr = fp2 * (dlj - dli);
     else
         rr = fp2 * fmaf(oi.w, dlj, -(J.m * dli));
@@ -120,17 +136,19 @@ __device__ __forceinline__ void rotate_block_adj(JAdj &J, const float4 (&oi)[IPL
     }
 }
 
-// j sums of a block to the float64 totals acc[c N + slot], c = U0 U1 U2 V X0 X1 X2 G.
-template <bool GM>
+// j sums of a block to the float64 totals acc[c N + slot], c = U0 U1 U2 V X0 X1 X2 G
+// (the W form: W0 W1 W2).
+template <bool GM, bool EQ>
 __device__ __forceinline__ void flush_adj(const JAdj &J, double *acc, int64_t N)
 {
+    constexpr int NC = adj_nacc(GM ? ADJOINT_GM : ADJOINT, EQ);
     if (J.slot < 0) return;
-    if (J.u0 == 0.f && J.u1 == 0.f && J.u2 == 0.f && J.v == 0.f && J.x0 == 0.f && J.x1 == 0.f && J.x2 == 0.f &&
-        (!GM || J.g == 0.f))
+    if (J.u0 == 0.f && J.u1 == 0.f && J.u2 == 0.f &&
+        (NC == 3 || (J.v == 0.f && J.x0 == 0.f && J.x1 == 0.f && J.x2 == 0.f)) && (!GM || J.g == 0.f))
         return;
     const float c[8] = {J.u0, J.u1, J.u2, J.v, J.x0, J.x1, J.x2, J.g};
 #pragma unroll
-    for (int k = 0; k < (GM ? 8 : 7); ++k) atomicAdd(acc + k * N + J.slot, (double)c[k]);
+    for (int k = 0; k < NC; ++k) atomicAdd(acc + k * N + J.slot, (double)c[k]);
 }
 
 // One task (sub-chunk): i particles [ib, ie) against their own chunk, the
@@ -161,7 +179,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
         oi[u] = active[u] ? a.pos[i] : make_float4(FAR, FAR, FAR, 0.f);
         li[u] = active[u] ? a.lam[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    AccAdj<MODE, IPL> A(comp, lane);
+    AccAdj<MODE, IPL, adj_nacc(MODE, EQ)> A(comp, lane);
 
     if constexpr (HALF) {  // the chunk against itself on the low half-warp, 16 steps
         const bool lo = lane < 16;
@@ -172,18 +190,18 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
             J.m = J.lx = J.ly = J.lz = 0.f;
         }
         rotate_block_adj<1, GM, EQ, 1u, 0u, 16>(J, oi, li, K, A.p, lane);
-        flush_adj<GM>(J, acc, N);
+        flush_adj<GM, EQ>(J, acc, N);
         A.fold();
     } else {  // the chunk against itself
         JAdj J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, li[0].x, li[0].y, li[0].z,
                0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[0] ? ib + lane : -1};
         rotate_block_adj<IPL, GM, EQ, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, li, K, A.p, lane);
-        flush_adj<GM>(J, acc, N);
+        flush_adj<GM, EQ>(J, acc, N);
         if constexpr (IPL == 2) {
             JAdj J1{oi[1].x, oi[1].y, oi[1].z, oi[1].w, li[1].x, li[1].y, li[1].z,
                     0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[1] ? ib + 32 + lane : -1};
             rotate_block_adj<IPL, GM, EQ, 2u, 0u>(J1, oi, li, K, A.p, lane);
-            flush_adj<GM>(J1, acc, N);
+            flush_adj<GM, EQ>(J1, acc, N);
         }
         A.fold();
     }
@@ -258,7 +276,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
                     oo += take;
                 }
                 rotate_block_adj<IPL, GM, EQ, 0u, 0u, W>(J, oi, li, K, A.p, lane);
-                flush_adj<GM>(J, acc, N);
+                flush_adj<GM, EQ>(J, acc, N);
             }
             A.fold();
             ++ring.consumed;
@@ -271,7 +289,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
         if (!active[u]) continue;
         const int i = ib + il + 32 * u;  // HALF: both lanes of i add their part
 #pragma unroll
-        for (int k = 0; k < (GM ? 8 : 7); ++k)
+        for (int k = 0; k < A.NACC; ++k)
             atomicAdd(acc + k * N + i, (double)A.hi(u, k) + (double)A.lo(u, k));
     }
     return true;
@@ -324,8 +342,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
     }
 }
 
-// dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V + X)) and
-// dL/dm_k = -G from the float64 totals, in input order.
+// dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V + X); the W
+// form: m_k W) and dL/dm_k = -G from the float64 totals, in input order.
 __global__ void __launch_bounds__(256)
 k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm,
                  const float4 *__restrict__ pos, const float4 *__restrict__ lam, const uint32_t *mass_varies,
@@ -335,6 +353,12 @@ k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__res
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[k];
         const double m = (double)pos[k].w;
+        if (eq && !gm) {
+            gx[i] = (float)(m * acc[k]);
+            gy[i] = (float)(m * acc[N + k]);
+            gz[i] = (float)(m * acc[2 * N + k]);
+            continue;
+        }
         const float4 l = lam[k];
         const double V = acc[3 * N + k];
         if (eq) {

@@ -122,7 +122,8 @@ __device__ __forceinline__ float rsqrt_hw(float x)
     return y;
 }
 
-// Adjoint accumulator layout (sizes the adjoint's shared memory).
+// Adjoint accumulator layout (sizes the adjoint's shared memory): room for
+// two i per lane with eight sums each (four i with the W form's three fit).
 constexpr int ADJ_NACC = 8;
 constexpr int ADJ_IPL_MAX = 2;
 constexpr int ADJ_COMP_BYTES = ADJ_IPL_MAX * ADJ_NACC * 2 * 32 * 4;
@@ -143,6 +144,7 @@ __host__ __device__ constexpr int adj_nacc(int mode, bool eq)
 template <int MODE, int IPL, int NC = adj_nacc(MODE, false)>
 struct AccAdj {
     static constexpr int NACC = NC;
+    static_assert(IPL * NC <= ADJ_IPL_MAX * ADJ_NACC, "compensated sums exceed the shared-memory slots");
     float p[IPL][ADJ_NACC];
     float *comp;  // [IPL][NACC][hi, lo][32 lanes]
     int lane;

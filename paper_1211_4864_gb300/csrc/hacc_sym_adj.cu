@@ -151,6 +151,21 @@ __device__ __forceinline__ void flush_adj(const JAdj &J, double *acc, int64_t N)
     for (int k = 0; k < NC; ++k) atomicAdd(acc + k * N + J.slot, (double)c[k]);
 }
 
+// The chunk's own block B (its i set B as the j): sets below B meet every j,
+// set B the upper triangle, the sets above none (they meet set B's records
+// when their own block comes round).
+template <int B, int IPL, bool GM, bool EQ>
+__device__ __forceinline__ void own_block_adj(const float4 (&oi)[IPL], const float4 (&li)[IPL],
+                                              const bool (&active)[IPL], int ib, int lane, const PairConsts &K,
+                                              float (&p)[IPL][ADJ_NACC], double *acc, int64_t N)
+{
+    constexpr unsigned SKIP = (0xFu << (B + 1)) & ((1u << IPL) - 1u);
+    JAdj J{oi[B].x, oi[B].y, oi[B].z, oi[B].w, li[B].x, li[B].y, li[B].z,
+           0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[B] ? ib + 32 * B + lane : -1};
+    rotate_block_adj<IPL, GM, EQ, 1u << B, SKIP>(J, oi, li, K, p, lane);
+    flush_adj<GM, EQ>(J, acc, N);
+}
+
 // One task (sub-chunk): i particles [ib, ie) against their own chunk, the
 // rest of the cell and the forward half of the list.  HALF (at most 16
 // particles): each i in lanes l and l + 16, the half-warps rotate the two
@@ -193,15 +208,11 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
         flush_adj<GM, EQ>(J, acc, N);
         A.fold();
     } else {  // the chunk against itself
-        JAdj J{oi[0].x, oi[0].y, oi[0].z, oi[0].w, li[0].x, li[0].y, li[0].z,
-               0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[0] ? ib + lane : -1};
-        rotate_block_adj<IPL, GM, EQ, 1u, (IPL == 2 ? 2u : 0u)>(J, oi, li, K, A.p, lane);
-        flush_adj<GM, EQ>(J, acc, N);
-        if constexpr (IPL == 2) {
-            JAdj J1{oi[1].x, oi[1].y, oi[1].z, oi[1].w, li[1].x, li[1].y, li[1].z,
-                    0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, active[1] ? ib + 32 + lane : -1};
-            rotate_block_adj<IPL, GM, EQ, 2u, 0u>(J1, oi, li, K, A.p, lane);
-            flush_adj<GM, EQ>(J1, acc, N);
+        own_block_adj<0, IPL, GM, EQ>(oi, li, active, ib, lane, K, A.p, acc, N);
+        if constexpr (IPL >= 2) own_block_adj<1, IPL, GM, EQ>(oi, li, active, ib, lane, K, A.p, acc, N);
+        if constexpr (IPL >= 4) {
+            own_block_adj<2, IPL, GM, EQ>(oi, li, active, ib, lane, K, A.p, acc, N);
+            own_block_adj<3, IPL, GM, EQ>(oi, li, active, ib, lane, K, A.p, acc, N);
         }
         A.fold();
     }
@@ -324,9 +335,15 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
         bool ok = true;
-        for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
-            const int se = min(sb + 64, task.z);
-            if (se - sb > 32)
+        // sub-chunks of larger tasks: 128 particles (four i per lane) in the W form,
+        // whose three sums leave the registers for it, else 64
+        constexpr int CHUNK = adj_wform(GM ? ADJOINT_GM : ADJOINT, EQ) ? 128 : 64;
+        for (int sb = task.y; ok && sb < task.z; sb += CHUNK) {
+            const int se = min(sb + CHUNK, task.z);
+            if (CHUNK == 128 && se - sb > 64)
+                ok = run_task_adj_sym<JT, STAGES, (CHUNK == 128 ? 4 : 2), GM, EQ>(a, ring, comp, acc, N, lane,
+                                                                                  task.x, sb, se, vol);
+            else if (se - sb > 32)
                 ok = run_task_adj_sym<JT, STAGES, 2, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);
             else if (se - sb > 16)
                 ok = run_task_adj_sym<JT, STAGES, 1, GM, EQ>(a, ring, comp, acc, N, lane, task.x, sb, se, vol);

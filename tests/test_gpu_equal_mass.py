@@ -158,3 +158,30 @@ def test_adjoints_against_oracle(hs, kernel, masses, want_gm):
     if want_gm:
         grms = np.linalg.norm(gm.cpu().numpy() - rgm) / np.linalg.norm(rgm)
         assert grms < RMS_TOL, grms
+
+
+@pytest.mark.parametrize("split_T", [128, 97, 65])
+def test_symmetric_adjoint_four_per_lane(hs, split_T):
+    """Equal masses without dL/dm: the symmetric adjoint runs tasks of 65 to
+    128 particles with four i per lane (the chunk's own four blocks, then the
+    half stencil).  Against the float64 adjoint and the gather adjoint."""
+    import torch
+    w = clustered_box(18, 5, seed=29)
+    n = w.x.size
+    rng = np.random.default_rng(37)
+    w = with_masses(w, np.full(n, 0.37))
+    lam = rng.normal(size=(n, 3)).astype(np.float32)
+    sr = prepare(hs, w, split_T=split_T)
+    sizes = np.diff(sr.tasks.cpu().numpy()[: int(sr.n_tasks.item()), 1:3], axis=1).ravel()
+    assert sizes.max() > 64  # the four-per-lane path runs
+    prm = params(hs)
+    lt = torch.tensor(lam.T.copy(), device="cuda")
+    g_s, _ = sr.adjoint_symmetric(prm, lt, want_gm=False)
+    g_g, _ = sr.adjoint(prm, lt, want_gm=False)
+    torch.cuda.synchronize()
+    sr.check_status()
+    rg, _ = oracle.sr_force_adjoint(w.x, w.y, w.z, w.m, float(w.L[0]), EPS, RC,
+                                    default_coeffs(RC, EPS).astype(np.float64), lam)
+    for name, g in (("symmetric", g_s), ("gather", g_g)):
+        rms, _ = err_norms(g.cpu().numpy().T, rg)
+        assert rms < RMS_TOL, (name, rms)

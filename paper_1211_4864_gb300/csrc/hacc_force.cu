@@ -152,8 +152,9 @@ __device__ __forceinline__ void tile_potential(const float4 *__restrict__ tj, in
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
 // Equal masses (EQ): V += f and X += fp2 (d.(lam_j - lam_i)) d, so that
 // dL/dx_i = m (U - lam_i V + X); one dot product instead of two without G.
-// Equal masses without G (the W form): the three sums fold into one,
-// W += f (lam_j - lam_i) + fp2 (d.(lam_j - lam_i)) d, and dL/dx_i = m W.
+// Without G (the W form) the three sums fold into one: with mu = m_i lam_j -
+// m_j lam_i, W += f mu + fp2 (d.mu) d and dL/dx_i = W (equal masses: mu / m
+// summed, dL/dx_i = m W).
 // One pair of the adjoint, accumulated into acc[8] = (U, V, X, G) of one i
 // (the W form: acc[3] = W).
 template <bool GM, bool EQ>
@@ -171,8 +172,17 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
     float f = t3 + q;
     float qp = fmaf(fmaf(fmaf(fmaf(K.kp[4], se, K.kp[3]), se, K.kp[2]), se, K.kp[1]), se, K.kp[0]);
     float fp2 = fmaf(-3.0f, t3 * t2, qp);
-    if constexpr (EQ && !GM) {
-        const float ex = l.x - lix, ey = l.y - liy, ez = l.z - liz;
+    if constexpr (!GM) {
+        float ex, ey, ez;  // mu (equal masses: mu / m)
+        if constexpr (EQ) {
+            ex = l.x - lix;
+            ey = l.y - liy;
+            ez = l.z - liz;
+        } else {
+            ex = fmaf(mi, l.x, -(p.w * lix));
+            ey = fmaf(mi, l.y, -(p.w * liy));
+            ez = fmaf(mi, l.z, -(p.w * liz));
+        }
         const float r = fp2 * fmaf(dz, ez, fmaf(dy, ey, dx * ex));
         asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %3, %4;\n\t"
             "@p fma.rn.f32 %0, %5, %6, %0;\n\t@p fma.rn.f32 %1, %5, %7, %1;\n\t@p fma.rn.f32 %2, %5, %8, %2;\n\t"
@@ -191,25 +201,15 @@ __device__ __forceinline__ void pair_adjoint(const float4 p, const float4 l, flo
     }
     const float mj = EQ ? 1.0f : p.w;
     // the accumulations of this pair happen only inside the cutoff
-    if constexpr (GM) {
-        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
-            "@p fma.rn.f32 %0, %10, %11, %0;\n\t@p fma.rn.f32 %1, %10, %12, %1;\n\t@p fma.rn.f32 %2, %10, %13, %2;\n\t"
-            "@p fma.rn.f32 %3, %14, %10, %3;\n\t"
-            "@p fma.rn.f32 %4, %15, %16, %4;\n\t@p fma.rn.f32 %5, %15, %17, %5;\n\t@p fma.rn.f32 %6, %15, %18, %6;\n\t"
-            "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
-            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]),
-              "+f"(acc[7])
-            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(mj), "f"(r), "f"(dx), "f"(dy),
-              "f"(dz), "f"(dlj));
-    } else {
-        asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %7, %8;\n\t"
-            "@p fma.rn.f32 %0, %9, %10, %0;\n\t@p fma.rn.f32 %1, %9, %11, %1;\n\t@p fma.rn.f32 %2, %9, %12, %2;\n\t"
-            "@p fma.rn.f32 %3, %13, %9, %3;\n\t"
-            "@p fma.rn.f32 %4, %14, %15, %4;\n\t@p fma.rn.f32 %5, %14, %16, %5;\n\t@p fma.rn.f32 %6, %14, %17, %6;\n\t}"
-            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6])
-            : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(mj), "f"(r), "f"(dx), "f"(dy),
-              "f"(dz));
-    }
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.f32 p, %8, %9;\n\t"
+        "@p fma.rn.f32 %0, %10, %11, %0;\n\t@p fma.rn.f32 %1, %10, %12, %1;\n\t@p fma.rn.f32 %2, %10, %13, %2;\n\t"
+        "@p fma.rn.f32 %3, %14, %10, %3;\n\t"
+        "@p fma.rn.f32 %4, %15, %16, %4;\n\t@p fma.rn.f32 %5, %15, %17, %5;\n\t@p fma.rn.f32 %6, %15, %18, %6;\n\t"
+        "@p fma.rn.f32 %7, %10, %19, %7;\n\t}"
+        : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]),
+          "+f"(acc[7])
+        : "f"(se), "f"(K.rc2e), "f"(f), "f"(l.x), "f"(l.y), "f"(l.z), "f"(mj), "f"(r), "f"(dx), "f"(dy),
+          "f"(dz), "f"(dlj));
 }
 
 // Adjoint pair loop over one staged tile (positions tj, cotangents tl).
@@ -217,7 +217,7 @@ template <int MODE, int IPL, bool EQ>
 __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, const float4 *__restrict__ tl, int n,
                                              const float (&op)[IPL][3], const float4 (&oi)[IPL],
                                              const float4 (&li)[IPL], const PairConsts &K,
-                                             AccAdj<MODE, IPL, adj_nacc(MODE, EQ)> &A)
+                                             AccAdj<MODE, IPL, adj_nacc(MODE)> &A)
 {
     constexpr bool GM = MODE == ADJOINT_GM;
     int j = 0;
@@ -248,7 +248,7 @@ __device__ __forceinline__ auto make_acc(float *comp, int lane)
     if constexpr (MODE == FORCE || MODE == POTENTIAL)
         return Acc<MODE, IPL>();
     else
-        return AccAdj<MODE, IPL, adj_nacc(MODE, EQ)>(comp, lane);
+        return AccAdj<MODE, IPL, adj_nacc(MODE)>(comp, lane);
 }
 
 // One task: i particles [ib, ie) of cell c (at most 32 IPL of them), every
@@ -410,11 +410,12 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             // the sum met particle i itself once (d = 0, se = eps exactly): take that term out
             const float self = pair_potential_of(K.eps, K);
             a.out_x[o] = (A.h[u][0] + A.l[u][0]) - oi[u].w * self;
-        } else if constexpr (adj_wform(MODE, EQ)) {
-            // dL/dx_i = m W
-            a.out_x[o] = oi[u].w * A.total(u, 0);
-            a.out_y[o] = oi[u].w * A.total(u, 1);
-            a.out_z[o] = oi[u].w * A.total(u, 2);
+        } else if constexpr (adj_wform(MODE)) {
+            // dL/dx_i = W (equal masses: m W)
+            const float sc = EQ ? oi[u].w : 1.0f;
+            a.out_x[o] = sc * A.total(u, 0);
+            a.out_y[o] = sc * A.total(u, 1);
+            a.out_z[o] = sc * A.total(u, 2);
         } else {
             // dL/dx_i = m_i U - lam_i V + X (equal masses: m (U - lam_i V + X)) ;  dL/dm_i = -G
             const float Vs = A.total(u, 3);

@@ -130,18 +130,16 @@ constexpr int ADJ_COMP_BYTES = ADJ_IPL_MAX * ADJ_NACC * 2 * 32 * 4;
 
 // Adjoint accumulators per i particle: U (3) = sum f lam_j, V = sum m_j f,
 // X (3) = sum fp2 (m_i d.lam_j - m_j d.lam_i) d, G = sum f d.lam_j (with dL/dm
-// only).  With equal masses and without dL/dm (the W form) the three sums
-// collapse into one vector, W (3) = sum f (lam_j - lam_i) + fp2 (d.(lam_j -
-// lam_i)) d, and dL/dx_i = m W.  Float32 partial sums live in registers for
-// one tile; the compensated (hi, lo) totals live in shared memory,
-// lane-contiguous, so that two i particles per lane fit the register budget.
-__host__ __device__ constexpr bool adj_wform(int mode, bool eq) { return eq && mode == ADJOINT; }
-__host__ __device__ constexpr int adj_nacc(int mode, bool eq)
-{
-    return mode == ADJOINT_GM ? 8 : (adj_wform(mode, eq) ? 3 : 7);
-}
+// only).  Without dL/dm (the W form) the three sums collapse into one
+// vector: with mu = m_i lam_j - m_j lam_i, W (3) = sum f mu + fp2 (d.mu) d =
+// dL/dx_i (equal masses: mu / m summed, dL/dx_i = m W).  Float32 partial sums
+// live in registers for one tile; the compensated (hi, lo) totals live in
+// shared memory, lane-contiguous, so that two i particles per lane fit the
+// register budget.
+__host__ __device__ constexpr bool adj_wform(int mode) { return mode == ADJOINT; }
+__host__ __device__ constexpr int adj_nacc(int mode) { return mode == ADJOINT_GM ? 8 : (adj_wform(mode) ? 3 : 7); }
 
-template <int MODE, int IPL, int NC = adj_nacc(MODE, false)>
+template <int MODE, int IPL, int NC = adj_nacc(MODE)>
 struct AccAdj {
     static constexpr int NACC = NC;
     static_assert(IPL * NC <= ADJ_IPL_MAX * ADJ_NACC, "compensated sums exceed the shared-memory slots");

@@ -17,10 +17,10 @@ namespace {
 // d_k = x_p - x_k, so that dL/dx_k = m_k U - lam_k V + X and dL/dm_k = -G.
 // For the pair seen from j every term flips sign or swaps: U_j += f lam_i,
 // V_j += m_i f, X_j -= r d, G_j -= f d.lam_i.
-// Equal masses without dL/dm (the W form): the pair's whole term
-// w = f (lam_j - lam_i) + fp2 (d.(lam_j - lam_i)) d is antisymmetric, like a
-// force, so i adds w and j subtracts it; each side carries three sums (u0,
-// u1, u2) and dL/dx_k = m W_k.
+// Without dL/dm (the W form): with mu = m_i lam_j - m_j lam_i the pair's
+// whole term w = f mu + fp2 (d.mu) d is antisymmetric, like a force, so i
+// adds w and j subtracts it; each side carries three sums (u0, u1, u2) and
+// dL/dx_k = W_k (equal masses: mu / m summed, dL/dx_k = m W_k).
 // ---------------------------------------------------------------------------
 
 // One j of an adjoint rotation block: record shifted into the i frame, its
@@ -34,7 +34,7 @@ struct JAdj {
 template <bool GM, bool EQ>
 __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
 {
-    constexpr bool WF = adj_wform(GM ? ADJOINT_GM : ADJOINT, EQ);
+    constexpr bool WF = adj_wform(GM ? ADJOINT_GM : ADJOINT);
     J.x = __shfl_sync(FULL, J.x, src);
     J.y = __shfl_sync(FULL, J.y, src);
     J.z = __shfl_sync(FULL, J.z, src);
@@ -56,7 +56,8 @@ __device__ __forceinline__ void rotate_adj(JAdj &J, int src)
 // One pair of the adjoint, both sides; outside the cutoff (or outside the
 // upper triangle of a diagonal block) f and r are zero, so every sum is
 // unchanged.  Equal masses (EQ): V sums f on both sides and r = fp2
-// d.(lam_j - lam_i), the common mass applied by the finishing pass.
+// d.(lam_j - lam_i) (the W form: mu / m), the common mass applied by the
+// finishing pass.
 template <bool GM, bool EQ>
 __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const float4 &li, const PairConsts &K,
                                              float (&acc)[ADJ_NACC], bool ok)
@@ -72,8 +73,17 @@ __device__ __forceinline__ void pair_adj_sym(JAdj &J, const float4 &oi, const fl
     const float fp2 = fmaf(-3.0f, t3 * t2, qp);
     const bool in = ok & (se < K.rc2e);
     const float f = in ? t3 + q : 0.0f;
-    if constexpr (EQ && !GM) {  // the W form
-        const float ex = J.lx - li.x, ey = J.ly - li.y, ez = J.lz - li.z;
+    if constexpr (!GM) {  // the W form
+        float ex, ey, ez;  // mu (equal masses: mu / m)
+        if constexpr (EQ) {
+            ex = J.lx - li.x;
+            ey = J.ly - li.y;
+            ez = J.lz - li.z;
+        } else {
+            ex = fmaf(oi.w, J.lx, -(J.m * li.x));
+            ey = fmaf(oi.w, J.ly, -(J.m * li.y));
+            ez = fmaf(oi.w, J.lz, -(J.m * li.z));
+        }
         const float r = in ? fp2 * fmaf(dz, ez, fmaf(dy, ey, dx * ex)) : 0.0f;
         const float wx = fmaf(f, ex, r * dx), wy = fmaf(f, ey, r * dy), wz = fmaf(f, ez, r * dz);
         acc[0] += wx;
@@ -141,7 +151,7 @@ __device__ __forceinline__ void rotate_block_adj(JAdj &J, const float4 (&oi)[IPL
 template <bool GM, bool EQ>
 __device__ __forceinline__ void flush_adj(const JAdj &J, double *acc, int64_t N)
 {
-    constexpr int NC = adj_nacc(GM ? ADJOINT_GM : ADJOINT, EQ);
+    constexpr int NC = adj_nacc(GM ? ADJOINT_GM : ADJOINT);
     if (J.slot < 0) return;
     if (J.u0 == 0.f && J.u1 == 0.f && J.u2 == 0.f &&
         (NC == 3 || (J.v == 0.f && J.x0 == 0.f && J.x1 == 0.f && J.x2 == 0.f)) && (!GM || J.g == 0.f))
@@ -194,7 +204,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
         oi[u] = active[u] ? a.pos[i] : make_float4(FAR, FAR, FAR, 0.f);
         li[u] = active[u] ? a.lam[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    AccAdj<MODE, IPL, adj_nacc(MODE, EQ)> A(comp, lane);
+    AccAdj<MODE, IPL, adj_nacc(MODE)> A(comp, lane);
 
     if constexpr (HALF) {  // the chunk against itself on the low half-warp, 16 steps
         const bool lo = lane < 16;
@@ -337,7 +347,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
         bool ok = true;
         // sub-chunks of larger tasks: 128 particles (four i per lane) in the W form,
         // whose three sums leave the registers for it, else 64
-        constexpr int CHUNK = adj_wform(GM ? ADJOINT_GM : ADJOINT, EQ) ? 128 : 64;
+        constexpr int CHUNK = adj_wform(GM ? ADJOINT_GM : ADJOINT) ? 128 : 64;
         for (int sb = task.y; ok && sb < task.z; sb += CHUNK) {
             const int se = min(sb + CHUNK, task.z);
             if (CHUNK == 128 && se - sb > 64)
@@ -360,7 +370,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
 }
 
 // dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V + X); the W
-// form: m_k W) and dL/dm_k = -G from the float64 totals, in input order.
+// form: W, equal masses m_k W) and dL/dm_k = -G from the float64 totals, in
+// input order.
 __global__ void __launch_bounds__(256)
 k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm,
                  const float4 *__restrict__ pos, const float4 *__restrict__ lam, const uint32_t *mass_varies,
@@ -370,10 +381,11 @@ k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__res
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[k];
         const double m = (double)pos[k].w;
-        if (eq && !gm) {
-            gx[i] = (float)(m * acc[k]);
-            gy[i] = (float)(m * acc[N + k]);
-            gz[i] = (float)(m * acc[2 * N + k]);
+        if (!gm) {  // the W form
+            const double sc = eq ? m : 1.0;
+            gx[i] = (float)(sc * acc[k]);
+            gy[i] = (float)(sc * acc[N + k]);
+            gz[i] = (float)(sc * acc[2 * N + k]);
             continue;
         }
         const float4 l = lam[k];
@@ -454,7 +466,7 @@ extern "C" int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc
     a.lam = F.lam;
     a.counter = F.counter;
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
-    HACC_CUDA_TRY(cudaMemsetAsync(F.acc, 0, (size_t)mesh->N * (gm ? 8 : 7) * sizeof(double), st));
+    HACC_CUDA_TRY(cudaMemsetAsync(F.acc, 0, (size_t)mesh->N * (gm ? 8 : 3) * sizeof(double), st));
     hacc_launch L;
     if (launch) {
         L = *launch;

@@ -161,17 +161,20 @@ def test_adjoints_against_oracle(hs, kernel, masses, want_gm):
 
 
 @pytest.mark.parametrize("split_T", [128, 97, 65])
-def test_symmetric_adjoint_four_per_lane(hs, split_T):
-    """Equal masses without dL/dm: the symmetric adjoint runs tasks of 65 to
-    128 particles with four i per lane (the chunk's own four blocks, then the
-    half stencil).  Against the float64 adjoint and the gather adjoint."""
+@pytest.mark.parametrize("masses", ["equal", "varied"])
+def test_symmetric_adjoint_four_per_lane(hs, split_T, masses):
+    """Without dL/dm (the single antisymmetric vector sum per pair) the
+    symmetric adjoint runs tasks of 65 to 128 particles with four i per lane
+    (the chunk's own four blocks, then the half stencil), on either mass path.
+    Against the float64 adjoint and the gather adjoint."""
     import torch
     w = clustered_box(18, 5, seed=29)
     n = w.x.size
     rng = np.random.default_rng(37)
-    w = with_masses(w, np.full(n, 0.37))
+    w = with_masses(w, np.full(n, 0.37) if masses == "equal" else rng.uniform(0.5, 2.0, n))
     lam = rng.normal(size=(n, 3)).astype(np.float32)
     sr = prepare(hs, w, split_T=split_T)
+    assert flag(sr) == (0 if masses == "equal" else 1)
     sizes = np.diff(sr.tasks.cpu().numpy()[: int(sr.n_tasks.item()), 1:3], axis=1).ravel()
     assert sizes.max() > 64  # the four-per-lane path runs
     prm = params(hs)

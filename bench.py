@@ -33,21 +33,20 @@ if ROOT not in sys.path:
 
 FLOPS_PER_PAIR = 29  # FMA = 2, add/mul = 1; rsqrt and the select not counted
 FLOPS_PER_PAIR_EQ = 28  # equal-mass path: no x m_j
-# DRAM bytes of one force launch on clustered256, from ncu (profiles/force_clustered256_dram.md),
-# valid only for the kernel source it was measured on
 # flops per evaluated unordered pair of the symmetric kernel: d 3, s 5, s + eps 1, t^3 2, Horner 10,
 # subtract 1, x m_j and x m_i 2, both accumulations 12
 FLOPS_PER_SYM_PAIR = 36
 FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
-# ncu DRAM bytes (read + write) of one force launch on clustered256, per kernel, with the sources
-# they were taken from (null in the bench line once a source changes)
+# ncu DRAM bytes (read + write) per force launch on clustered256 (mean over the launches of one
+# capture, profiles/force_clustered256_dram.md), per kernel, with the sources they were taken
+# from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2221459456 + 966782208,
+    "gather": {"workload": "clustered256", "bytes": 2215281920 + 963089280,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "40962c6002c7f1679c570ca48baf21394977c86d52b4064efecc1ff3f93eaf95"},
-    "symmetric": {"workload": "clustered256", "bytes": 2792153856 + 1488596480,
+               "sha256": "7aeaa3826cb1540cbe0e9d488c18bb9d8bbd01222df7a8e0c8ca8b54cce916e2"},
+    "symmetric": {"workload": "clustered256", "bytes": 2794192025 + 1488052787,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
-                  "sha256": "7b5c9fe81dfb3efe0942d83116bd638af25458d80dd8e5524ba5e7689f7785b2"},
+                  "sha256": "c8bc8a395869e2da83c6ff2de0bc87b15d6c0527b0e5087ec76e9ae147656c17"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

@@ -436,7 +436,8 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
 
 // Persistent work-stealing kernel: each warp takes tasks from a global
 // counter until none is left.  A task of more than 32 particles runs two i
-// particles per lane, one of at most 16 runs each i on two lanes.
+// particles per lane (four, above 64, in the adjoint's W form), one of at most
+// 16 runs each i on two lanes.
 // Register budgets: the forward and potential kernels keep 80 registers so that
 // 3 CTAs (24 warps) fit an SM; the adjoint's staging needs twice the shared
 // memory, which caps it at 2 CTAs, so it may use up to 128 registers.
@@ -479,9 +480,15 @@ __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
         const int4 task = a.tasks[a.order[t]];
         const hacc_volume &vol = a.vols[task.w];
         bool ok = true;
-        for (int sb = task.y; ok && sb < task.z; sb += 64) {  // 64-particle sub-chunks of larger tasks
-            const int se = min(sb + 64, task.z);
-            if (se - sb > 32)
+        // sub-chunks of larger tasks: 128 particles (four i per lane) for the adjoint's W form,
+        // whose three sums leave the registers for it, else 64
+        constexpr int CHUNK = adj_wform(MODE) ? 128 : 64;
+        for (int sb = task.y; ok && sb < task.z; sb += CHUNK) {
+            const int se = min(sb + CHUNK, task.z);
+            if (CHUNK == 128 && se - sb > 64)
+                ok = run_task<MODE, JT, STAGES, (CHUNK == 128 ? 4 : 2), EQ>(a, ring, comp, lane, task.x, sb, se,
+                                                                             vol);
+            else if (se - sb > 32)
                 ok = run_task<MODE, JT, STAGES, 2, EQ>(a, ring, comp, lane, task.x, sb, se, vol);
             else
                 ok = run_task<MODE, JT, STAGES, 1, EQ>(a, ring, comp, lane, task.x, sb, se, vol);

@@ -41,10 +41,10 @@ FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
 # capture, profiles/force_clustered256_dram.md), per kernel, with the sources they were taken
 # from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2215281920 + 963089280,
+    "gather": {"workload": "clustered256", "bytes": 2216422208 + 963080576,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "7aeaa3826cb1540cbe0e9d488c18bb9d8bbd01222df7a8e0c8ca8b54cce916e2"},
-    "symmetric": {"workload": "clustered256", "bytes": 2794192025 + 1488052787,
+               "sha256": "213048a4259385d7c1317b462df3ddb585b843d1cb08e2719e94b7489d18f14c"},
+    "symmetric": {"workload": "clustered256", "bytes": 2796637132 + 1489595443,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
                   "sha256": "c8bc8a395869e2da83c6ff2de0bc87b15d6c0527b0e5087ec76e9ae147656c17"},
 }

@@ -44,9 +44,9 @@ FORCE_TRAFFIC = {
     "gather": {"workload": "clustered256", "bytes": 2216422208 + 963080576,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
                "sha256": "213048a4259385d7c1317b462df3ddb585b843d1cb08e2719e94b7489d18f14c"},
-    "symmetric": {"workload": "clustered256", "bytes": 2796637132 + 1489595443,
+    "symmetric": {"workload": "clustered256", "bytes": 2794154598 + 1487683584,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
-                  "sha256": "c8bc8a395869e2da83c6ff2de0bc87b15d6c0527b0e5087ec76e9ae147656c17"},
+                  "sha256": "fe7b6cdde8e806d03c4e4de705a650e3e954bb9031dd39b44a03bac755c2666f"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"

@@ -439,17 +439,17 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc
     }
 }
 
-// float64 totals (sorted slots) to float32 accelerations in input order.
+// One component of the float64 totals (sorted slots) to float32 in input
+// order.  The stores scatter through the permutation, 4 bytes each; they merge
+// into whole sectors in L2 only while the target array stays resident there,
+// which one 67 MB component per launch does and three at once do not (each
+// partial sector is then read and written back in DRAM).  The streamed totals
+// and perm are loaded evict-first for the same reason.
 __global__ void __launch_bounds__(256)
-k_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm, float *__restrict__ ax,
-             float *__restrict__ ay, float *__restrict__ az)
+k_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm, float *__restrict__ out)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        const int i = perm[k];
-        ax[i] = (float)acc[k];
-        ay[i] = (float)acc[N + k];
-        az[i] = (float)acc[2 * N + k];
-    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[__ldcs(perm + k)] = (float)__ldcs(acc + k);
 }
 
 template <int JT, int STAGES, bool EQ>
@@ -522,7 +522,10 @@ extern "C" int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned 
     if (rc) return rc;
     int g = (int)((mesh->N + 255) / 256);
     if (g > num_sms() * 16) g = num_sms() * 16;
-    k_sym_finish<<<g, 256, 0, st>>>(mesh->N, F.acc, binned->perm, ax, ay, az);
-    HACC_LAUNCH_CHECK();
+    float *out[3] = {ax, ay, az};
+    for (int c = 0; c < 3; ++c) {
+        k_sym_finish<<<g, 256, 0, st>>>(mesh->N, F.acc + c * mesh->N, binned->perm, out[c]);
+        HACC_LAUNCH_CHECK();
+    }
     return HACC_OK;
 }

@@ -369,9 +369,21 @@ __global__ void __launch_bounds__(256, 2) k_adj_sym(const KArgs a, double *acc, 
     }
 }
 
-// dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V + X); the W
-// form: W, equal masses m_k W) and dL/dm_k = -G from the float64 totals, in
-// input order.
+// The W form: one component of dL/dx = W (equal masses: m W, m the common
+// mass) from the float64 totals, in input order; one component per launch
+// for the reason given at k_sym_finish.
+__global__ void __launch_bounds__(256)
+k_adj_sym_finish_w(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm,
+                   const float4 *__restrict__ pos, const uint32_t *mass_varies, float *__restrict__ out)
+{
+    const bool eq = mass_varies && *mass_varies == 0u;
+    const double sc = eq ? (double)pos[0].w : 1.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[__ldcs(perm + k)] = (float)(sc * __ldcs(acc + k));
+}
+
+// With dL/dm: dL/dx_k = m_k U - lam_k V + X (equal masses: m_k (U - lam_k V +
+// X)) and dL/dm_k = -G from the float64 totals, in input order.
 __global__ void __launch_bounds__(256)
 k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__restrict__ perm,
                  const float4 *__restrict__ pos, const float4 *__restrict__ lam, const uint32_t *mass_varies,
@@ -381,13 +393,6 @@ k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__res
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const int i = perm[k];
         const double m = (double)pos[k].w;
-        if (!gm) {  // the W form
-            const double sc = eq ? m : 1.0;
-            gx[i] = (float)(sc * acc[k]);
-            gy[i] = (float)(sc * acc[N + k]);
-            gz[i] = (float)(sc * acc[2 * N + k]);
-            continue;
-        }
         const float4 l = lam[k];
         const double V = acc[3 * N + k];
         if (eq) {
@@ -399,7 +404,7 @@ k_adj_sym_finish(int64_t N, const double *__restrict__ acc, const int32_t *__res
             gy[i] = (float)(m * acc[N + k] - (double)l.y * V + acc[5 * N + k]);
             gz[i] = (float)(m * acc[2 * N + k] - (double)l.z * V + acc[6 * N + k]);
         }
-        if (gm) gm[i] = (float)(-acc[7 * N + k]);
+        gm[i] = (float)(-acc[7 * N + k]);
     }
 }
 
@@ -478,8 +483,18 @@ extern "C" int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc
     }
     rc = gm ? launch_adj_sym<true>(a, F.acc, mesh->N, L, st) : launch_adj_sym<false>(a, F.acc, mesh->N, L, st);
     if (rc) return rc;
-    k_adj_sym_finish<<<g, 256, 0, st>>>(mesh->N, F.acc, binned->perm, reinterpret_cast<const float4 *>(binned->sorted4),
-                                        F.lam, binned->mass_varies, gx, gy, gz, gm);
-    HACC_LAUNCH_CHECK();
+    const float4 *pos = reinterpret_cast<const float4 *>(binned->sorted4);
+    if (gm) {
+        k_adj_sym_finish<<<g, 256, 0, st>>>(mesh->N, F.acc, binned->perm, pos, F.lam, binned->mass_varies, gx, gy,
+                                            gz, gm);
+        HACC_LAUNCH_CHECK();
+        return HACC_OK;
+    }
+    float *out[3] = {gx, gy, gz};
+    for (int c = 0; c < 3; ++c) {
+        k_adj_sym_finish_w<<<g, 256, 0, st>>>(mesh->N, F.acc + c * mesh->N, binned->perm, pos, binned->mass_varies,
+                                              out[c]);
+        HACC_LAUNCH_CHECK();
+    }
     return HACC_OK;
 }

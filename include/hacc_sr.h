@@ -99,8 +99,9 @@ typedef struct hacc_binned {
                             it to 0 when every mass is bitwise equal to the first particle's (N = 0
                             included) and to 1 otherwise.  When it reads 0, the force calls
                             (hacc_sr_force, hacc_sr_force_symmetric) and the adjoint calls take
-                            their equal-mass path: the pair sums hold f d (adjoint: V = sum f,
-                            X = sum 2 f' (d.(lam_j - lam_i)) d) and each particle's total is
+                            their equal-mass path: the pair sums hold f d (adjoint without gm:
+                            W = sum f (lam_j - lam_i) + 2 f' (d.(lam_j - lam_i)) d; with gm:
+                            V = sum f, X = sum 2 f' (d.(lam_j - lam_i)) d) and each particle's total is
                             scaled once by its own mass, the common m (sum_j m_j f d =
                             m sum_j f d), which saves per-pair mass products; the results agree
                             with the general path to float32 rounding.  NULL: the general path,
@@ -335,8 +336,9 @@ int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned *binned, co
 
 /* hacc_sr_force_adjoint with each pair evaluated once: the pair's terms of
  * dL/dx are antisymmetric (J(d) is even in d), so the j side receives minus
- * the i side's, and both sides keep the factored sums U, V, X, G of the
- * gather adjoint (float64 totals by atomics, as hacc_sr_force_symmetric).
+ * the i side's: one vector sum W per particle when gm is NULL, the factored
+ * sums U, V, X, G of the gather adjoint otherwise (float64 totals by atomics,
+ * as hacc_sr_force_symmetric).
  * Same arguments and outputs as hacc_sr_force_adjoint; chaining-mesh or
  * tree lists; not bitwise reproducible.  Not in the paper. */
 int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc_binned *binned,
@@ -350,7 +352,10 @@ int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc_binned *bi
  *   gx_i = dL/dx_i = sum_j [m_i J(d_ij) lam_j - m_j J(d_ij) lam_i],
  *   J(d) = f_SR(s) I + 2 f_SR'(s) d d^T,
  *   gm_i = dL/dm_i = -sum_j f_SR(s_ij) d_ij . lam_j        (gm may be NULL),
- * recomputing every pair term (nothing is stored by the forward call). */
+ * recomputing every pair term (nothing is stored by the forward call).  With
+ * gm NULL each pair adds J(d_ij) mu_ij, mu_ij = m_i lam_j - m_j lam_i, to one
+ * vector sum; with gm the kernel keeps the sums U = sum f lam_j, V = sum m_j f,
+ * X = sum 2 f' (m_i d.lam_j - m_j d.lam_i) d and G (gx = m_i U - lam_i V + X). */
 int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *binned,
                           const hacc_lists *lists, const hacc_sr_params *p, const float *gax,
                           const float *gay, const float *gaz, float *gx, float *gy, float *gz,

@@ -265,6 +265,35 @@ def test_adjoint_against_torch_float64_autograd():
     assert np.allclose(gm, M.grad.numpy(), rtol=1e-10, atol=1e-10)
 
 
+def test_adjoint_as_one_antisymmetric_sum():
+    """Without dL/dm the gradient is one vector sum per particle: with
+    mu_ij = m_i lam_j - m_j lam_i and J(d) = f I + 2 f' d d^T, the pair adds
+    w_ij = J(d_ij) mu_ij to dL/dx_i, and w_ji = -w_ij (the form the GPU adjoints
+    sum; equal masses: m sum_j J(d_ij) (lam_j - lam_i)).  Dense numpy float64
+    against the oracle's adjoint."""
+    c = default_coeffs().astype(np.float64)
+    rng = np.random.default_rng(23)
+    L, N = 7.0, 80
+    p = rng.random((N, 3)) * L
+    lam = rng.normal(size=(N, 3))
+    d = p[None, :, :] - p[:, None, :]  # d[i, j] = x_j - x_i, minimal image
+    d -= L * np.round(d / L)
+    s = (d * d).sum(-1)
+    mask = (s < RC * RC) & ~np.eye(N, dtype=bool)
+    f = np.where(mask, (s + EPS) ** -1.5 - np.polyval(c[::-1], s), 0.0)
+    dc = np.arange(1, 6) * c[1:]
+    fp2 = np.where(mask, 2.0 * (-1.5 * (s + EPS) ** -2.5 - np.polyval(dc[::-1], s)), 0.0)
+    for m in (rng.uniform(0.5, 1.5, N), np.full(N, 0.37)):
+        mu = m[:, None, None] * lam[None, :, :] - m[None, :, None] * lam[:, None, :]
+        w = f[..., None] * mu + (fp2 * (d * mu).sum(-1))[..., None] * d
+        assert np.allclose(w, -w.transpose(1, 0, 2), rtol=0, atol=1e-12)
+        gx, _ = oracle.sr_force_adjoint(p[:, 0], p[:, 1], p[:, 2], m, L, EPS, RC, c, lam)
+        assert np.allclose(w.sum(1), gx, rtol=1e-10, atol=1e-10)
+    dl = lam[None, :, :] - lam[:, None, :]
+    we = f[..., None] * dl + (fp2 * (d * dl).sum(-1))[..., None] * d
+    assert np.allclose(0.37 * we.sum(1), gx, rtol=1e-10, atol=1e-10)
+
+
 def test_trajectory_gradient_against_finite_differences():
     from oracle import diff
     c = default_coeffs().astype(np.float64)

@@ -41,9 +41,9 @@ FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
 # capture, profiles/force_clustered256_dram.md), per kernel, with the sources they were taken
 # from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2216422208 + 963080576,
+    "gather": {"workload": "clustered256", "bytes": 2216940416 + 964173632,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "213048a4259385d7c1317b462df3ddb585b843d1cb08e2719e94b7489d18f14c"},
+               "sha256": "04360c7de1f51bd350abc5c81fffcae6239dea46664d8bcc33e87ec3fea8d6f4"},
     "symmetric": {"workload": "clustered256", "bytes": 2794154598 + 1487683584,
                   "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
                   "sha256": "fe7b6cdde8e806d03c4e4de705a650e3e954bb9031dd39b44a03bac755c2666f"},

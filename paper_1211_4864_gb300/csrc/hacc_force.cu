@@ -151,7 +151,7 @@ __device__ __forceinline__ void tile_potential(const float4 *__restrict__ tj, in
 // X += fp2 (m_i (d.lam_j) - m_j (d.lam_i)) d ;  G += f (d.lam_j).
 // Then dL/dx_i = m_i U - lam_i V + X and dL/dm_i = -G.
 // Equal masses (EQ): V += f and X += fp2 (d.(lam_j - lam_i)) d, so that
-// dL/dx_i = m (U - lam_i V + X); one dot product instead of two without G.
+// dL/dx_i = m (U - lam_i V + X).
 // Without G (the W form) the three sums fold into one: with mu = m_i lam_j -
 // m_j lam_i, W += f mu + fp2 (d.mu) d and dL/dx_i = W (equal masses: mu / m
 // summed, dL/dx_i = m W).
@@ -242,7 +242,7 @@ __device__ __forceinline__ void tile_adjoint(const float4 *__restrict__ tj, cons
 
 
 
-template <int MODE, int IPL, bool EQ>
+template <int MODE, int IPL>
 __device__ __forceinline__ auto make_acc(float *comp, int lane)
 {
     if constexpr (MODE == FORCE || MODE == POTENTIAL)
@@ -287,7 +287,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             if (active[u]) li[u] = a.lam[ib + il + 32 * u];
         }
     }
-    auto A = make_acc<MODE, IPL, EQ>(comp, lane);
+    auto A = make_acc<MODE, IPL>(comp, lane);
 
     const int64_t e0 = a.nbr_off[c], e1 = a.nbr_off[c + 1];
     for (int64_t g0 = e0; g0 < e1; g0 += 32) {

@@ -37,9 +37,8 @@ FLOPS_PER_PAIR_EQ = 28  # equal-mass path: no x m_j
 # subtract 1, x m_j and x m_i 2, both accumulations 12
 FLOPS_PER_SYM_PAIR = 36
 FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
-# ncu DRAM bytes (read + write) per force launch on clustered256 (mean over the launches of one
-# capture, profiles/force_clustered256_dram.md), per kernel, with the sources they were taken
-# from (null in the bench line once a source changes)
+# ncu DRAM bytes (read + write) per force launch on clustered256, per kernel, with the sources
+# they were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
     "gather": {"workload": "clustered256", "bytes": 2216940416 + 964173632,
                "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
@@ -321,27 +320,29 @@ def run_ours(args):
         pass
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * 128 * 2 * f_max * 1e6 / 1e12
-    # algorithmic work (the roofline's numerator): FLOPS_PER_PAIR per evaluated interaction, i.e. per
-    # ordered candidate pair the step's force covers, whichever kernel covers it; the flops the
-    # kernel's FP32 pipe actually executes are reported beside it
-    achieved = FLOPS_PER_PAIR * pairs / (t_force * 1e-3) / 1e12
+    # the roofline's numerator: the flops the kernel executes per evaluated pair times the pairs it
+    # evaluates in one launch.  The gather kernel evaluates every ordered candidate pair; the
+    # symmetric kernel evaluates each unordered pair once and applies it to both particles, so it
+    # evaluates half the interactions the step covers (with both accumulations in its flop count).
     if args.kernel == "symmetric":
-        executed = fpp_s * (pairs / 2) / (t_force * 1e-3) / 1e12  # each unordered pair evaluated once
+        evaluated = pairs // 2
+        fpp = fpp_s
         kname = "k_pairs_sym (hacc_sr_force_symmetric)"
-        ex = {"flops_per_unordered_pair": fpp_s, "unordered_pairs": pairs // 2}
     else:
-        executed = fpp_g * pairs / (t_force * 1e-3) / 1e12
+        evaluated = pairs
+        fpp = fpp_g
         kname = "k_pairs<FORCE> (hacc_sr_force)"
-        ex = {"flops_per_pair": fpp_g}
+    achieved = fpp * evaluated / (t_force * 1e-3) / 1e12
+    strict = FLOPS_PER_PAIR * evaluated / (t_force * 1e-3) / 1e12
     out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved,
                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                        "traffic": force_traffic(args.config, args.kernel),
-                       "algorithmic_flops_per_interaction": FLOPS_PER_PAIR, "interactions": pairs,
+                       "flops_per_evaluated_pair": fpp, "evaluated_pairs_per_launch": evaluated,
+                       "interactions_per_launch": pairs,
+                       "mass_path": "equal (every particle mass equal)" if eq else "general (per-particle masses)",
                        "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {f_max:.0f} MHz (max SM clock)",
                        "force_ms": t_force, "force_share": t_force / (t_ms / args.steps),
-                       "executed": {"achieved": executed, "frac": executed / peak, **ex,
-                                    "mass_path": "equal (every particle mass equal)" if eq
-                                    else "general (per-particle masses)"}}
+                       "frac_at_29_flops_per_evaluated_pair": strict / peak}
     if clk.get("sm_mhz"):
         out["roofline"]["frac_at_measured_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
 
@@ -551,10 +552,8 @@ def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak,
     rel = float((a.double() - b.double()).norm() / b.double().norm())
     return {"gather_force_ms": t_g, "symmetric_force_ms": t_s, "speedup": t_g / t_s,
             "interactions_per_s": {"gather": pairs / (t_g * 1e-3), "symmetric": pairs / (t_s * 1e-3)},
-            "fp32_frac_executed": {"gather": fpp_g * pairs / (t_g * 1e-3) / 1e12 / peak,
-                                   "symmetric": fpp_s * pairs / 2 / (t_s * 1e-3) / 1e12 / peak},
-            "fp32_frac_algorithmic": {"gather": FLOPS_PER_PAIR * pairs / (t_g * 1e-3) / 1e12 / peak,
-                                      "symmetric": FLOPS_PER_PAIR * pairs / (t_s * 1e-3) / 1e12 / peak},
+            "fp32_frac": {"gather": fpp_g * pairs / (t_g * 1e-3) / 1e12 / peak,
+                          "symmetric": fpp_s * (pairs // 2) / (t_s * 1e-3) / 1e12 / peak},
             "force_rel_diff": rel,
             "launch": {"gather": launch.__dict__ if launch else "default",
                        "symmetric": launch_sym.__dict__ if launch_sym else "default"}}
@@ -591,9 +590,9 @@ def mass_paths(torch, sr, pos, m, prm, lam, launches, a, pairs, peak, eq_ms, rep
     sr.set_equal_mass_path(True)
     sr.prepare(pos, m)
     torch.cuda.synchronize()
-    t["fp32_frac_executed"] = {
+    t["fp32_frac"] = {
         "gather": FLOPS_PER_PAIR * pairs / (t["gather_force_ms"] * 1e-3) / 1e12 / peak,
-        "symmetric": FLOPS_PER_SYM_PAIR * pairs / 2 / (t["symmetric_force_ms"] * 1e-3) / 1e12 / peak}
+        "symmetric": FLOPS_PER_SYM_PAIR * (pairs // 2) / (t["symmetric_force_ms"] * 1e-3) / 1e12 / peak}
     return {"general": t,
             "equal_mass_speedup": {k: t[k] / eq_ms[k] for k in eq_ms},
             "force_rel_diff_equal_vs_general": rel}

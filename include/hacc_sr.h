@@ -140,6 +140,14 @@ typedef struct hacc_launch {
     int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid, 1..8 */
     int32_t jtile;         /* j particles per staged tile: 32, 64, 128 or 256 */
     int32_t stages;        /* staged tiles in flight per warp: 2..4 */
+    int64_t wait_cycles;   /* bound of each wait for a staged tile, in SM clock cycles (clock64),
+                              checked before every poll of the tile's mbarrier; 0 = the default
+                              2e9 (about 1 s at 2 GHz), negative is invalid.  A warp whose wait runs
+                              out sets HACC_STATUS_TIMEOUT, lets the copies it has in flight land
+                              (waiting at most the default bound), and stops taking tasks; the
+                              call's results are then invalid.  A bound of 1 makes every wait give
+                              up at once although its copies complete: the failure path can be
+                              exercised without a hang. */
 } hacc_launch;
 
 /* Library version and build target, e.g. "hacc_sr 1 sm_103a". Host. */

@@ -66,11 +66,12 @@ class hacc_sr_params(ctypes.Structure):
 
 class hacc_launch(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("jtile", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("jtile", ctypes.c_int32), ("stages", ctypes.c_int32), ("wait_cycles", ctypes.c_int64)]
 
 
 assert ctypes.sizeof(hacc_volume) == 64
 assert ctypes.sizeof(hacc_mesh) == 40
+assert ctypes.sizeof(hacc_launch) == 24
 
 _P = ctypes.c_void_p
 _PS = ctypes.POINTER

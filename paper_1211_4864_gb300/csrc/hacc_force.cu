@@ -323,7 +323,7 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
         int cur = -1;
         float op[IPL][3];
         while (ring.consumed < ring.issued) {
-            if (!ring.wait_next()) return false;
+            if (!ring.wait_next(a.wait_limit)) return false;
             const float4 *tj = ring.tile(ring.consumed % STAGES);
             // replay the producer's pieces: each piece is one entry's records
             int filled = 0;
@@ -604,6 +604,7 @@ hacc_launch default_launch(int mode)
     L.ctas_per_sm = 3;
     L.jtile = mode == FORCE ? 64 : 64;
     L.stages = 4;
+    L.wait_cycles = 0;
     return L;
 }
 
@@ -634,6 +635,7 @@ extern "C" int hacc_sr_force(const hacc_mesh *mesh, const hacc_binned *binned, c
     a.counter = F.counter;
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(FORCE);
+    a.wait_limit = wait_limit_of(L);
     return launch_mode<FORCE>(a, L, st);
 }
 
@@ -662,6 +664,7 @@ extern "C" int hacc_sr_force_adjoint(const hacc_mesh *mesh, const hacc_binned *b
     a.counter = F.counter;
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(ADJOINT);
+    a.wait_limit = wait_limit_of(L);
     if (gm) return launch_mode<ADJOINT_GM>(a, L, st);
     return launch_mode<ADJOINT>(a, L, st);
 }
@@ -681,6 +684,7 @@ extern "C" int hacc_sr_potential(const hacc_mesh *mesh, const hacc_binned *binne
     a.counter = F.counter;
     HACC_CUDA_TRY(cudaMemsetAsync(F.counter, 0, sizeof(int32_t), st));
     hacc_launch L = launch ? *launch : default_launch(FORCE);
+    a.wait_limit = wait_limit_of(L);
     return launch_mode<POTENTIAL>(a, L, st);
 }
 

@@ -13,7 +13,7 @@ namespace hacc {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // default wait bound: ~1 s at 2 GHz
 constexpr uint32_t WAIT_HINT_NS = 100000;  // a waiting warp may sleep up to 0.1 ms per try
 
 // FORCE: accelerations.  ADJOINT: dL/dx.  ADJOINT_GM: dL/dx and dL/dm.
@@ -48,6 +48,7 @@ struct KArgs {
     uint32_t *status;
     PairConsts k;
     const uint32_t *mass_varies;  // 0: every mass equal (the equal-mass force paths); NULL: general
+    long long wait_limit;         // bound of each tile wait, clock64 cycles
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -90,15 +91,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// All lanes wait for a barrier phase; false (uniformly) if it ran out of time.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity)
+// All lanes wait for a barrier phase; false (uniformly) once the wait has
+// lasted `limit` clock64 cycles of lane 0, checked before every poll.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long limit)
 {
-    long long t0 = clock64();
+    const long long t0 = clock64();
     while (true) {
-        uint32_t ok = mbar_try_wait(bar, parity);
-        if (__all_sync(FULL, ok)) return true;
-        int late = (clock64() - t0) > WAIT_LIMIT_CYCLES;
+        const int late = (clock64() - t0) >= limit;
         if (__shfl_sync(FULL, late, 0)) return false;
+        const uint32_t ok = mbar_try_wait(bar, parity);
+        if (__all_sync(FULL, ok)) return true;
     }
 }
 
@@ -249,16 +251,17 @@ struct Ring {
         return true;
     }
     // bounded wait for the next tile; false if the wait ran out
-    __device__ __forceinline__ bool wait_next() const
+    __device__ __forceinline__ bool wait_next(long long limit) const
     {
         const uint32_t st = consumed % STAGES;
-        return warp_wait(bar(st), (consumed / STAGES) & 1u);
+        return warp_wait(bar(st), (consumed / STAGES) & 1u, limit);
     }
-    // after a timeout: let the copies still in flight land (bounded) before leaving
+    // after a timeout: let the copies still in flight land before leaving, each
+    // wait bounded by the default limit whatever bound gave up
     __device__ __forceinline__ void drain()
     {
         while (consumed < issued) {
-            warp_wait(bar(consumed % STAGES), (consumed / STAGES) & 1u);
+            warp_wait(bar(consumed % STAGES), (consumed / STAGES) & 1u, WAIT_LIMIT_CYCLES);
             ++consumed;
         }
     }
@@ -341,7 +344,7 @@ int check_common(const hacc_mesh *mesh, const hacc_binned *b, const hacc_lists *
     if (l->split_T < 1 || l->split_T > 128) return HACC_ERR_INVALID;
     if (launch) {
         if (launch->warps_per_cta < 1 || launch->warps_per_cta > 8 || launch->ctas_per_sm < 1 ||
-            launch->ctas_per_sm > 8)
+            launch->ctas_per_sm > 8 || launch->wait_cycles < 0)
             return HACC_ERR_INVALID;
     }
     if (ws_bytes < force_layout(mesh, nullptr).total) return HACC_ERR_CAPACITY;
@@ -366,9 +369,13 @@ KArgs base_args(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lis
     a.perm = binned->perm;
     a.mass_varies = binned->mass_varies;
     a.status = status;
+    a.wait_limit = WAIT_LIMIT_CYCLES;
     pair_consts(p, a.k);
     return a;
 }
+
+// The wait bound a launch asks for (0: the default).
+long long wait_limit_of(const hacc_launch &L) { return L.wait_cycles > 0 ? (long long)L.wait_cycles : WAIT_LIMIT_CYCLES; }
 
 }  // namespace
 }  // namespace hacc

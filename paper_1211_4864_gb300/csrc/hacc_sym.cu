@@ -311,7 +311,7 @@ __device__ __forceinline__ bool run_task_sym(const KArgs &a, Ring<FORCE, JT, STA
         for (int s = 0; s < STAGES; ++s)
             if (!ring.produce(a, lane, ng, cnt, jb, pk, poff)) break;
         while (ring.consumed < ring.issued) {
-            if (!ring.wait_next()) return false;
+            if (!ring.wait_next(a.wait_limit)) return false;
             const float4 *tj = ring.tile(ring.consumed % STAGES);
             // the producer's pieces again: piece start in the tile, source slot, image offset
             int filled = 0;
@@ -517,7 +517,9 @@ extern "C" int hacc_sr_force_symmetric(const hacc_mesh *mesh, const hacc_binned 
         L.ctas_per_sm = 3;
         L.jtile = 128;
         L.stages = 2;
+        L.wait_cycles = 0;
     }
+    a.wait_limit = wait_limit_of(L);
     rc = launch_sym(a, F.acc, mesh->N, L, st);
     if (rc) return rc;
     int g = (int)((mesh->N + 255) / 256);

@@ -250,7 +250,7 @@ __device__ __forceinline__ bool run_task_adj_sym(const KArgs &a, Ring<ADJOINT, J
         for (int s = 0; s < STAGES; ++s)
             if (!ring.produce(a, lane, ng, cnt, jb, pk, poff)) break;
         while (ring.consumed < ring.issued) {
-            if (!ring.wait_next()) return false;
+            if (!ring.wait_next(a.wait_limit)) return false;
             const float4 *tj = ring.tile(ring.consumed % STAGES);
             int filled = 0;
             const int k_first = ck, off_first = coff;
@@ -480,7 +480,9 @@ extern "C" int hacc_sr_force_adjoint_symmetric(const hacc_mesh *mesh, const hacc
         L.ctas_per_sm = 2;
         L.jtile = 128;
         L.stages = 2;
+        L.wait_cycles = 0;
     }
+    a.wait_limit = wait_limit_of(L);
     rc = gm ? launch_adj_sym<true>(a, F.acc, mesh->N, L, st) : launch_adj_sym<false>(a, F.acc, mesh->N, L, st);
     if (rc) return rc;
     const float4 *pos = reinterpret_cast<const float4 *>(binned->sorted4);

@@ -64,9 +64,10 @@ class Launch:
     ctas_per_sm: int = 2
     jtile: int = 64
     stages: int = 4
+    wait_cycles: int = 0  # bound of each tile wait in SM cycles; 0 = the library default (~1 s)
 
     def c_struct(self) -> hacc_launch:
-        return hacc_launch(self.warps_per_cta, self.ctas_per_sm, self.jtile, self.stages)
+        return hacc_launch(self.warps_per_cta, self.ctas_per_sm, self.jtile, self.stages, self.wait_cycles)
 
 
 # ---------------------------------------------------------------------------

@@ -8,13 +8,16 @@ could contain.  All on the CPU (the mistakes are planted in the oracle only).
 import ctypes
 import os
 import subprocess
+import types
 
 import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_sks_pins as sks_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hacc_oracle.c")
+SKS_SRC = os.path.join(os.path.dirname(oracle.__file__), "sks.py")
 
 # (name, text in the oracle source, replacement)
 MUTANTS = [
@@ -52,6 +55,13 @@ MUTANTS = [
     ("rcb leaf size off by one", "if (cnt <= S->leaf_max || depth", "if (cnt < S->leaf_max || depth"),
     ("rcb image shift sign", "double jlo = (double)(leaf_qbox[6 * j + a] - 1) * scale + (double)sh[a] * (double)L;",
      "double jlo = (double)(leaf_qbox[6 * j + a] - 1) * scale - (double)sh[a] * (double)L;"),
+    ("list gap off by one", "double gx = abs(dx) > 1 ? (double)(abs(dx) - 1) : 0.0;",
+     "double gx = abs(dx) > 2 ? (double)(abs(dx) - 2) : 0.0;"),
+    ("list predicate not strict", "return (gx * gx + gy * gy + gz * gz) * w * w < rc * rc;",
+     "return (gx * gx + gy * gy + gz * gz) * w * w <= rc * rc;"),
+    ("rcb boxes widened twice", "double ilo = (double)(leaf_qbox[6 * i + a] - 1) * scale;",
+     "double ilo = (double)(leaf_qbox[6 * i + a] - 2) * scale;"),
+    ("rcb lists not strict", "if (d2 < rc2) {", "if (d2 <= rc2) {"),
     ("drift before kick", "        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += dt_d * vx[i];",
      "        if (x) x[i] += dt_d * vx[i];\n        vx[i] += dt_k * ax[i];\n        vy[i] += dt_k * ay[i];\n        vz[i] += dt_k * az[i];\n        if (x) {\n            x[i] += 0.0;"),
 ]
@@ -75,11 +85,15 @@ PINS = [
     pins.test_binning_invariants_and_numpy_restatement,
     pins.test_binning_with_displacements_keeps_float64_positions,
     lambda: pins.test_lists_cover_every_pair_within_cutoff(16.0, 3.0, 3.0),
+    lambda: pins.test_lists_are_exactly_the_cells_whose_boxes_come_closer_than_rc(9.0, 1.0, 3.0),
+    lambda: pins.test_lists_are_exactly_the_cells_whose_boxes_come_closer_than_rc(6.4, 0.375, 3.0),
     pins.test_rcb_hand_worked_examples,
     pins.test_rcb_regular_lattice_is_bit_interleaved,
     pins.test_rcb_leaves_invariants_on_clustered_particles,
     lambda: pins.test_rcb_lists_cover_every_pair_within_cutoff("uniform", 16),
     lambda: pins.test_rcb_lists_cover_every_pair_within_cutoff("clustered", 24),
+    lambda: pins.test_rcb_lists_are_exactly_the_leaves_whose_widened_boxes_come_closer("uniform", 16),
+    pins.test_rcb_lists_cutoff_is_strict_on_exact_gaps,
     pins.test_trajectory_gradient_against_finite_differences,
 ]
 
@@ -119,3 +133,55 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
 def test_unmutated_oracle_passes_every_pin():
     for pin in PINS:
         pin()
+
+
+# Planted mistakes in the sub-cycle reference (oracle/sks.py): the order and
+# length of the half-streams and the kick, the wrap, the energy factors.
+_S1 = "x = np.mod(x + 0.5 * h * v, L)\n        a = sr_force(x[:, 0], x[:, 1], x[:, 2], m, L, eps, rcut, c)"
+_K = "v = v + h * a\n        x = np.mod(x + 0.5 * h * v, L)\n        hist"
+SKS_MUTANTS = [
+    ("first stream by a full step", _S1, _S1.replace("0.5 * h * v", "h * v")),
+    ("force before the first stream", _S1,
+     "a = sr_force(x[:, 0], x[:, 1], x[:, 2], m, L, eps, rcut, c)\n        x = np.mod(x + 0.5 * h * v, L)"),
+    ("kick-stream-kick instead of stream-kick-stream", _S1 + "\n        " + _K,
+     "a = sr_force(x[:, 0], x[:, 1], x[:, 2], m, L, eps, rcut, c)\n        v = v + 0.5 * h * a\n"
+     "        x = np.mod(x + h * v, L)\n        a = sr_force(x[:, 0], x[:, 1], x[:, 2], m, L, eps, rcut, c)\n"
+     "        v = v + 0.5 * h * a\n        hist"),
+    ("second stream with the old velocity", _K,
+     "x = np.mod(x + 0.5 * h * v, L)\n        v = v + h * a\n        hist"),
+    ("kick by half a step", _K, _K.replace("v = v + h * a", "v = v + 0.5 * h * a")),
+    ("final stream not wrapped", _K, _K.replace("x = np.mod(x + 0.5 * h * v, L)", "x = x + 0.5 * h * v")),
+    ("kinetic energy without the half", "0.5 * np.sum(m[:, None] * v * v)", "np.sum(m[:, None] * v * v)"),
+    ("pair potential counted twice", "0.5 * np.sum(m * phi)", "np.sum(m * phi)"),
+]
+
+
+def _sks_module(src_text):
+    mod = types.ModuleType("oracle._sks_mutant")
+    mod.__package__ = "oracle"
+    exec(compile(src_text, "sks_mutant.py", "exec"), mod.__dict__)
+    return mod
+
+
+def test_every_planted_subcycle_mistake_fails_a_pin():
+    src = open(SKS_SRC).read()
+    survivors = []
+    for name, old, new in SKS_MUTANTS:
+        assert src.count(old) == 1, f"mutation site not found: {name}"
+        mod = _sks_module(src.replace(old, new, 1))
+        caught = False
+        for check in sks_pins.SKS_CHECKS:
+            try:
+                check(mod)
+            except Exception:
+                caught = True
+                break
+        if not caught:
+            survivors.append(name)
+    assert not survivors, f"sub-cycle mistakes no pin catches: {survivors}"
+
+
+def test_unmutated_subcycles_pass_every_pin():
+    mod = _sks_module(open(SKS_SRC).read())
+    for check in sks_pins.SKS_CHECKS:
+        check(mod)

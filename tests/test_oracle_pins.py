@@ -465,6 +465,52 @@ def test_lists_cover_every_pair_within_cutoff(L, cell_min, rcut):
         assert np.all(np.diff(off) == 27)
 
 
+def _interval_gap_d2(a0, a1, b0, b1):
+    """Squared distance between the closest points of two axis-aligned boxes
+    [a0, a1] and [b0, b1] (float64 arrays of 3 per box, leading axes
+    broadcast): the closest point of box a to box b's low corner, then the
+    closest point of box b to that point."""
+    pa = np.clip(b0, a0, a1)
+    pb = np.clip(pa, b0, b1)
+    return ((pb - pa) ** 2).sum(-1)
+
+
+@pytest.mark.parametrize("L,cell_min,rcut", [(10.0, 2.0, 3.0), (9.0, 1.0, 3.0), (6.4, 0.375, 3.0),
+                                             (16.0, 3.0, 3.0)])
+def test_lists_are_exactly_the_cells_whose_boxes_come_closer_than_rc(L, cell_min, rcut):
+    """Tightness: a neighbour (cell, image) is listed iff the two cell boxes
+    have points closer than r_c.  The boxes are laid out from the mesh's cell
+    width, the closest points found by projection, over a window one cell
+    wider than the stencil.  Meshes: reach 2, reach 3 with w = 1 (offsets
+    (3, 3, 2) leave gaps (2, 2, 1) w, exactly r_c, so a non-strict test would
+    list them), reach 8, and the 27-cell case."""
+    n, w, _ = oracle.mesh(L, cell_min)
+    R = oracle.reach(w, rcut)
+    off, cell, shift = oracle.lists_volume(n, w, rcut)
+    W = float(w)
+    win = np.array([(dx, dy, dz) for dz in range(-R - 1, R + 2) for dy in range(-R - 1, R + 2)
+                    for dx in range(-R - 1, R + 2)], np.int64)
+    rng = np.random.default_rng(3)
+    cells = {0, n ** 3 - 1, (n // 2) * (n * n + n + 1)} | set(rng.integers(0, n ** 3, 5).tolist())
+    for c in sorted(cells):
+        cc = np.array([c % n, (c // n) % n, c // (n * n)], np.int64)
+        got = set()
+        for e in range(off[c], off[c + 1]):
+            p = int(cell[e])
+            pc = np.array([p % n, (p // n) % n, p // (n * n)], np.int64)
+            code = int(shift[e])
+            sh = np.array([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], np.int64)
+            got.add(tuple((pc + sh * n - cc).tolist()))
+        assert len(got) == off[c + 1] - off[c]
+        lo_a = cc * W
+        lo_b = (cc + win) * W
+        d2 = _interval_gap_d2(lo_a, lo_a + W, lo_b, lo_b + W)
+        expect = {tuple(d.tolist()) for d in win[d2 < rcut * rcut]}
+        assert got == expect, (c, sorted(got ^ expect)[:6])
+    if (L, cell_min) == (9.0, 1.0):
+        assert (3, 3, 2) not in got and (3, 3, 1) in got
+
+
 def test_lists_reject_too_coarse_mesh():
     with pytest.raises(ValueError):
         oracle.lists_volume(4, 1.0, 3.0)   # R = 3 needs n >= 7
@@ -609,6 +655,56 @@ def test_rcb_lists_cover_every_pair_within_cutoff(maker, leaf_max):
     missing = [(a, b, c) for a, b, c in zip(leaf_of[ii], leaf_of[jj], code) if (a, b, c) not in listed]
     assert not missing, missing[:5]
     assert len(ii) > 1000
+
+
+def _rcb_expected_lists(qbox, L, rcut):
+    """Every (i, j, image code) whose leaf boxes, widened by one grid step on
+    every side, have points closer than r_c (closest points by projection)."""
+    q = np.asarray(qbox, np.float64)
+    step = L / 2 ** 21
+    lo = (q[:, :3] - 1) * step
+    hi = (q[:, 3:] + 2) * step
+    out = set()
+    for code in range(27):
+        sh = np.array([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], np.float64) * L
+        d2 = _interval_gap_d2(lo[:, None], hi[:, None], lo[None] + sh, hi[None] + sh)
+        ii, jj = np.nonzero(d2 < rcut * rcut)
+        out.update(zip(ii.tolist(), jj.tolist(), [code] * len(ii)))
+    return out
+
+
+@pytest.mark.parametrize("maker,leaf_max", [("uniform", 16), ("clustered", 24)])
+def test_rcb_lists_are_exactly_the_leaves_whose_widened_boxes_come_closer(maker, leaf_max):
+    """Tightness of the leaf lists: (leaf j, image) is listed for leaf i iff
+    the widened boxes have points closer than r_c, and nothing else is."""
+    from synth.workloads import clustered_box
+    w = uniform_box(1200, 12.0, seed=8) if maker == "uniform" else clustered_box(16, 2, seed=9)
+    L = float(w.L[0])
+    r = oracle.rcb_volume(w.x, w.y, w.z, w.m, L, leaf_max)
+    off, leaf, shift = oracle.rcb_lists(r["leaf_qbox"], L, RC)
+    got = set()
+    for i in range(r["n_leaves"]):
+        got.update((i, int(j), int(c)) for j, c in zip(leaf[off[i]:off[i + 1]], shift[off[i]:off[i + 1]]))
+    assert len(got) == off[-1]
+    assert got == _rcb_expected_lists(r["leaf_qbox"], L, RC)
+
+
+def test_rcb_lists_cutoff_is_strict_on_exact_gaps():
+    """Hand-made leaf boxes on a box of 16 (grid step 2^-17, exact in float64):
+    leaf 1's widened box starts exactly r_c = 3 beyond leaf 0's, leaf 2's one
+    step closer.  Only leaf 2 (and leaf 0 itself) may be listed for leaf 0,
+    and leaf 0 may not be listed for leaf 1 (the same gap seen from the right:
+    a box widened by more than one step on that side would list it)."""
+    L = 16.0
+    q0 = [0, 0, 0, 10, 10, 10]
+    g = 3 * 2 ** 17 + 13  # widened gap: (g - 1) - (10 + 2) steps = 3 * 2^17 steps = 3.0
+    q1 = [g, 0, 0, g + 10, 10, 10]
+    q2 = [g - 1, 20, 0, g + 9, 30, 10]
+    off, leaf, shift = oracle.rcb_lists(np.array([q0, q1, q2], np.int32), L, RC, targets=[0, 1])
+    ent0 = set(zip(leaf[off[0]:off[1]].tolist(), shift[off[0]:off[1]].tolist()))
+    ent1 = set(zip(leaf[off[1]:off[2]].tolist(), shift[off[1]:off[2]].tolist()))
+    assert ent0 == {(0, 13), (2, 13)}
+    assert ent1 == {(1, 13), (2, 13)}
 
 
 # --------------------------------------------------------------------------

@@ -204,13 +204,16 @@ int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float 
  * (inside a captured stream, a host callback, a real-time loop).  The scratch
  * space that hacc_bin takes as `ws` is instead one fixed array that the
  * library places in device memory when it is loaded: HACC_BIN_NOALLOC_BYTES
- * (9 MiB), enough for up to 262,144 particles (in any number of cells); every
- * device that loads the library keeps it until the process exits.  Larger
- * problems return HACC_ERR_CAPACITY (use hacc_bin with a workspace).  The
- * caller still passes the inputs and the outputs in `out`; nothing is
- * allocated or freed, by this library or any other.
+ * (9 MiB); every device that loads the library keeps it until the process
+ * exits.  A problem fits when hacc_bin_workspace_size(mesh) is at most that,
+ * about 20 bytes per particle plus 8 per cell (262,144 particles in up to
+ * 500,000 cells); larger problems return HACC_ERR_CAPACITY (use hacc_bin with
+ * a workspace).  The caller still passes the inputs and the outputs in `out`;
+ * nothing is allocated or freed, by this library or any other.
  * The first call on each device looks up the array's device address, with
- * that device current; make that first call before any stream capture.
+ * that device current; make that first call before any stream capture (a
+ * first call on a stream that is being captured returns HACC_ERR_INVALID and
+ * leaves the capture intact).
  * All calls share the one array: calls whose work overlaps on the GPU (on
  * different streams, or from several host threads) race and must be
  * serialised by the caller.  Each call clears the scratch it relies on, so

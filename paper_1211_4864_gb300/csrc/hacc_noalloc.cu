@@ -7,8 +7,8 @@
 
 namespace {
 
-// HACC_BIN_NOALLOC_BYTES (9 MiB): hacc_bin's scratch for up to 262,144
-// particles in up to 65,536 cells.
+// HACC_BIN_NOALLOC_BYTES (9 MiB): hacc_bin's scratch, about 20 bytes per
+// particle and 8 per cell (262,144 particles in up to 500,000 cells).
 constexpr size_t NOALLOC_BIN_BYTES = HACC_BIN_NOALLOC_BYTES;
 
 // Loaded with the library onto every device that runs it, and held until the
@@ -21,13 +21,21 @@ void *g_scratch_addr[MAX_DEVICES] = {};
 
 // Device address of g_bin_scratch on the current device.  In host code the
 // symbol's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and remembered.
-int scratch_address(void **out)
+// once per device (with that device current) and remembered.  The lookup is
+// refused while `st` is being captured into a graph: it would break the
+// capture.
+int scratch_address(cudaStream_t st, void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return HACC_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return HACC_ERR_CUDA;
+        }
+        if (cap != cudaStreamCaptureStatusNone) return HACC_ERR_INVALID;
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || !p) {
             (void)cudaGetLastError();
@@ -47,7 +55,7 @@ extern "C" int hacc_bin_noalloc(const hacc_mesh *mesh, const float *x, const flo
     if (!mesh) return HACC_ERR_INVALID;
     if (hacc_bin_workspace_size(mesh) > NOALLOC_BIN_BYTES) return HACC_ERR_CAPACITY;
     void *ws = nullptr;
-    int rc = scratch_address(&ws);
+    int rc = scratch_address(hacc::as_stream(stream), &ws);
     if (rc) return rc;
     // hacc_bin clears the cell counts it accumulates and overwrites every
     // other scratch word before reading it, so the previous call's contents

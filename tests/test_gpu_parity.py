@@ -125,6 +125,25 @@ def test_bin_lists_tasks_bit_exact_uniform(torch, hs):
     check_bin_lists(torch, hs, make_config("uniform4096"), 3.0, 3.0)
 
 
+@pytest.mark.parametrize("N", [200, 3000, 40000, 70000])
+def test_bin_bit_exact_when_one_cell_holds_most_particles(torch, hs, N):
+    """Degenerate clustering: most particles in one cell, the rest uniform.
+    The crowded cell takes each sorting path of the binning: 200 the warp's
+    shared-memory network, the others the block radix passes (index digits:
+    two significant bytes plus a copy pass at 3000 and 40000, three at
+    70000)."""
+    rng = np.random.default_rng(N)
+    L = np.float32(27.0)
+    k = N * 9 // 10
+    p = np.concatenate([rng.random((k, 3)) * 3.0 + 12.0, rng.random((N - k, 3)) * float(L)])
+    p = p[rng.permutation(N)].astype(np.float32)
+    w = Workload("crowded", p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), np.ones(N, np.float32),
+                 np.zeros(N, np.float32), np.zeros(N, np.float32), np.zeros(N, np.float32),
+                 np.array([L], np.float32), np.array([0, N], np.int64))
+    sr = check_bin_lists(torch, hs, w, 3.0, 3.0, split_T=128)
+    assert int(np.diff(sr.cell_start.cpu().numpy()).max()) >= k
+
+
 def test_bin_lists_bit_exact_fine_mesh_and_edge_positions(torch, hs):
     """Cells narrower than r_c (reach 2: 125-cell stencils), coordinates on
     and outside the box edges, a ragged split size."""

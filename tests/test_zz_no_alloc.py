@@ -63,3 +63,23 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     out = hacc_binned()
     rc = lib.hacc_bin_noalloc(ctypes.byref(mesh), None, None, None, None, ctypes.byref(out), None, None)
     assert rc == _lib.HACC_ERR_CAPACITY
+
+
+def test_noalloc_capacity_matches_the_documented_limit():
+    """The scratch array holds hacc_bin's workspace for 262,144 particles in
+    500,000 cells; one that needs more is refused with a capacity error on the
+    host, before any device work."""
+    from paper_1211_4864_gb300 import _lib
+    from paper_1211_4864_gb300._lib import hacc_binned, hacc_mesh
+    lib = _lib.load()
+    limit = 9 << 20
+    mesh = hacc_mesh()
+    mesh.V = 1
+    mesh.N = 262144
+    mesh.n_cells = 500000
+    assert lib.hacc_bin_workspace_size(ctypes.byref(mesh)) <= limit
+    mesh.n_cells = 600000
+    assert lib.hacc_bin_workspace_size(ctypes.byref(mesh)) > limit
+    out = hacc_binned()
+    rc = lib.hacc_bin_noalloc(ctypes.byref(mesh), None, None, None, None, ctypes.byref(out), None, None)
+    assert rc == _lib.HACC_ERR_CAPACITY

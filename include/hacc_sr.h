@@ -94,7 +94,8 @@ typedef struct hacc_binned {
     int32_t *perm;       /* [N] input index of the particle in sorted slot k */
     float *sorted4;      /* [4 N] per sorted slot (ox, oy, oz, m), o = cell-relative offset */
     float *cell_origin;  /* [4 n_cells] (x, y, z, 0) origin the offsets of each cell are taken from,
-                            or NULL for the chaining mesh (cell (cx, cy, cz) sits at float32 c w) */
+                            or NULL for the chaining mesh (the offsets of cell (cx, cy, cz) are taken
+                            from its centre, float32 (c + 1/2) w per axis) */
     uint32_t *mass_varies; /* device word or NULL.  hacc_bin, hacc_bin_noalloc and hacc_rcb_build set
                             it to 0 when every mass is bitwise equal to the first particle's (N = 0
                             included) and to 1 otherwise.  When it reads 0, the force calls
@@ -182,11 +183,12 @@ size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
  * three-phase structure-of-arrays partition (Sec. III), done as a stable
  * counting sort.  For particle i of volume v, per axis: xw = x - L floor(x/L)
  * (one correction step keeps xw in [0, L)), cell c = min(n-1, floor(xw inv_w)),
- * offset o = xw - c w, each a single float32 round-to-nearest operation.
+ * offset from the cell centre o = xw - fl32((c + 1/2) w) (|o| <= w/2), each a
+ * single float32 round-to-nearest operation.
  * Optional displacements dx, dy, dz (all three or none, [N]): the position is
  * then x + d, formed, wrapped and offset in float64 (same steps, each one
  * float64 round-to-nearest operation, the cell from floor(xw inv_w) in
- * float64) and only the offset o = xw - fl32(c w) is rounded to float32; a
+ * float64) and only the offset o = xw - fl32((c + 1/2) w) is rounded to float32; a
  * trajectory kept as a fixed reference plus a small drift displacement so
  * keeps its float64 position to float32 precision of a cell-relative offset.
  * Within a cell the sorted order is ascending input index (bit-exact and
@@ -411,7 +413,8 @@ int hacc_kick(const hacc_mesh *mesh, int64_t N, float *vx, float *vy, float *vz,
  * re-binning.  The lists stay complete while every particle stays within
  * skin/2 of its cell box, i.e. if they were built for r_c + skin (plan the
  * mesh with rcut = r_c + skin and cell_min >= r_c + skin): an offset outside
- * [-skin/2, w + skin/2) on any axis sets HACC_STATUS_SKIN, after which the
+ * [-(w + skin)/2, (w + skin)/2) (offsets are taken from the cell centre) on
+ * any axis sets HACC_STATUS_SKIN, after which the
  * caller must re-bin.  The input-order positions are not touched (drift them
  * with hacc_kick and no accelerations).  Not in the paper, whose sub-cycles
  * rebuild the tree walk each time. */

@@ -19,7 +19,8 @@
  * The chaining-mesh binning reference follows the float32 expression sequence
  * that defines a particle's cell (the build's reading of the paper's spatial
  * partition, Sec. III: a mesh replaces the RCB tree): wrap into [0, L), cell
- * index per axis, cell-relative offset.  Each step is a single IEEE float32
+ * index per axis, offset from the cell's centre (c + 1/2) w.  Each step is a
+ * single IEEE float32
  * operation with round-to-nearest; this file must be compiled with
  * -ffp-contract=off so that no step is fused.
  *
@@ -91,22 +92,24 @@ static int32_t cell64(double pw, float inv_w, int32_t n)
     return c;
 }
 
-/* Cell coordinate and cell-relative offset of one coordinate: float32 steps
- * for an absolute position; with a displacement d (non-NULL), the position
- * x + d is formed and wrapped in float64 and only the offset is rounded. */
+/* Cell coordinate and offset from the cell centre ctr = fl32((c + 1/2) w) of
+ * one coordinate: float32 steps for an absolute position; with a
+ * displacement d (non-NULL), the position x + d is formed and wrapped in
+ * float64 and only the offset is rounded. */
 static int32_t axis_cell(float x, const float *d, int64_t i, float L, int32_t n, float w, float inv_w,
                          float *o)
 {
     if (!d) {
         float xw = wrap32(x, L);
         int32_t c = cell1(xw, inv_w, n);
-        *o = xw - (float)c * w;
+        float ctr = ((float)c + 0.5f) * w;
+        *o = xw - ctr;
         return c;
     }
     double pw = wrap64((double)x + (double)d[i], (double)L);
     int32_t c = cell64(pw, inv_w, n);
-    float cw = (float)c * w;
-    *o = (float)(pw - (double)cw);
+    float ctr = ((float)c + 0.5f) * w;
+    *o = (float)(pw - (double)ctr);
     return c;
 }
 
@@ -122,8 +125,8 @@ static int32_t cell1(float xw, float inv_w, int32_t n)
 /* Binning of one volume.  Outputs: cell_of[i] (cell of particle i), counts per
  * cell, and the stable order: perm[k] = original index of the particle in
  * sorted slot k, particles ordered by cell and, within a cell, by original
- * index.  sorted4[4k..4k+3] = (ox, oy, oz, m) with o the cell-relative offset
- * (float32).  dx, dy, dz: optional displacements (all NULL for absolute
+ * index.  sorted4[4k..4k+3] = (ox, oy, oz, m) with o the offset from the
+ * cell centre (float32).  dx, dy, dz: optional displacements (all NULL for absolute
  * positions).  cell_start has n^3 + 1 entries.  Returns 0. */
 int ora_bin(const float *x, const float *y, const float *z, const float *dx, const float *dy,
             const float *dz, const float *m, int64_t N, float L, int32_t n, float w, float inv_w,

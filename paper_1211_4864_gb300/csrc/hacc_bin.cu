@@ -56,9 +56,11 @@ __device__ __forceinline__ int cell64(double pw, float inv_w, int n)
     return c < 0 ? 0 : c;
 }
 
-// One axis: cell coordinate and cell-relative offset.  Without a
-// displacement every step is float32; with one, the position x + d is formed
-// and wrapped in float64 and only the final offset is rounded to float32.
+// One axis: cell coordinate and offset from the cell centre
+// fl32((c + 1/2) w) (|o| <= w/2: half the rounding of a corner-relative
+// offset).  Without a displacement every step is float32; with one, the
+// position x + d is formed and wrapped in float64 and only the final offset
+// is rounded to float32.
 __device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, const hacc_volume &vol, float &o,
                                          uint32_t *status)
 {
@@ -67,12 +69,12 @@ __device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, con
     if (!d) {
         const float xw = wrap32(sanitize(x, status), L);
         const int c = cell1(xw, iw, n);
-        o = __fsub_rn(xw, __fmul_rn((float)c, w));
+        o = __fsub_rn(xw, cell_centre(c, w));
         return c;
     }
     const double pw = wrap64(__dadd_rn((double)sanitize(x, status), (double)sanitize(d[i], status)), (double)L);
     const int c = cell64(pw, iw, n);
-    o = __double2float_rn(__dsub_rn(pw, (double)__fmul_rn((float)c, w)));
+    o = __double2float_rn(__dsub_rn(pw, (double)cell_centre(c, w)));
     return c;
 }
 

@@ -54,6 +54,17 @@ __device__ __forceinline__ int cell1(float xw, float inv_w, int n)
     return c < 0 ? 0 : c;
 }
 
+// Centre of chaining-mesh cell c along one axis, fl32((c + 1/2) w): the
+// origin of the cell's offsets.
+__host__ __device__ __forceinline__ float cell_centre(int c, float w)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(__fadd_rn((float)c, 0.5f), w);
+#else
+    return ((float)c + 0.5f) * w;
+#endif
+}
+
 // Volume owning global index `key` in a monotone array of begins (binary search).
 __device__ __forceinline__ int find_volume_by_particle(const hacc_volume *vols, int V, int64_t i)
 {

@@ -310,10 +310,10 @@ __device__ __forceinline__ bool run_task(const KArgs &a, Ring<MODE, JT, STAGES> 
             } else {
                 const int64_t lp = (int64_t)cp - vol.cell_base;
                 const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-                // exact in float64: origins are the float32 products used by the binning
-                Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                // exact in float64: origins are the float32 cell centres used by the binning
+                Dx = (float)((double)cell_centre(px, w) - (double)cell_centre(cx, w) + sx * Ld);
+                Dy = (float)((double)cell_centre(py, w) - (double)cell_centre(cy, w) + sy * Ld);
+                Dz = (float)((double)cell_centre(pz, w) - (double)cell_centre(cz, w) + sz * Ld);
             }
         }
         int pk = 0, poff = 0;  // producer cursor (entry, record within it)
@@ -537,9 +537,9 @@ k_count_pairs(const KArgs a, unsigned long long *__restrict__ total)
                 } else {
                     const int64_t lp = (int64_t)cp - vol.cell_base;
                     const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-                    Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-                    Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-                    Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+                    Dx = (float)((double)cell_centre(px, w) - (double)cell_centre(cx, w) + sx * Ld);
+                    Dy = (float)((double)cell_centre(py, w) - (double)cell_centre(cy, w) + sy * Ld);
+                    Dz = (float)((double)cell_centre(pz, w) - (double)cell_centre(cz, w) + sz * Ld);
                 }
                 const float oxp = oi.x - Dx, oyp = oi.y - Dy, ozp = oi.z - Dz;
                 for (int j = a.cell_start[cp]; j < a.cell_start[cp + 1]; ++j) {

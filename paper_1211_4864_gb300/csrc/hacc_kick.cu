@@ -217,7 +217,7 @@ k_drift_offsets(int64_t N, const hacc_volume *__restrict__ vols, int V, const in
         r.y = fmaf(dt, vy[i], r.y);
         r.z = fmaf(dt, vz[i], r.z);
         sorted4[k] = r;
-        const float lo = -half_skin, hi = w + half_skin;
+        const float hi = __fadd_rn(0.5f * w, half_skin), lo = -hi;
         out |= !(r.x >= lo && r.x < hi && r.y >= lo && r.y < hi && r.z >= lo && r.z < hi);
     }
     if (__any_sync(0xffffffffu, out) && (threadIdx.x & 31) == 0) atomicOr(status, HACC_STATUS_SKIN);

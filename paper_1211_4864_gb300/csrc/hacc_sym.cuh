@@ -45,10 +45,10 @@ __device__ __forceinline__ void entry_delta(const KArgs &a, const hacc_volume &v
         const float w = vol.w;
         const int64_t lp = (int64_t)cp - vol.cell_base;
         const int px = (int)(lp % n), py = (int)((lp / n) % n), pz = (int)(lp / ((int64_t)n * n));
-        // exact in float64: origins are the float32 products used by the binning
-        Dx = (float)((double)__fmul_rn((float)px, w) - (double)__fmul_rn((float)cx, w) + sx * Ld);
-        Dy = (float)((double)__fmul_rn((float)py, w) - (double)__fmul_rn((float)cy, w) + sy * Ld);
-        Dz = (float)((double)__fmul_rn((float)pz, w) - (double)__fmul_rn((float)cz, w) + sz * Ld);
+        // exact in float64: origins are the float32 cell centres used by the binning
+        Dx = (float)((double)cell_centre(px, w) - (double)cell_centre(cx, w) + sx * Ld);
+        Dy = (float)((double)cell_centre(py, w) - (double)cell_centre(cy, w) + sy * Ld);
+        Dz = (float)((double)cell_centre(pz, w) - (double)cell_centre(cz, w) + sz * Ld);
     }
 }
 

@@ -42,7 +42,8 @@ MUTANTS = [
     ("wrap correction dropped", "    if (xw >= L) xw = xw - L;\n    return xw;", "    return xw;"),
     ("stencil row missing", "for (int dz = -R; dz <= R; ++dz)", "for (int dz = -R; dz < R; ++dz)"),
     ("image shift sign", "if (px < 0) { px += n; sx = -1; }", "if (px < 0) { px += n; sx = 1; }"),
-    ("cell origin offset", "*o = xw - (float)c * w;", "*o = xw - (float)(c + 1) * w;"),
+    ("cell origin offset", "float ctr = ((float)c + 0.5f) * w;\n        *o = xw - ctr;",
+     "float ctr = ((float)c + 1.5f) * w;\n        *o = xw - ctr;"),
     ("potential sign", "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) + 0.5 * P6(c, s));",
      "return (1.0 / sqrt(rc2 + eps) + 0.5 * P6(c, rc2)) - (1.0 / sqrt(s + eps) - 0.5 * P6(c, s));"),
     ("potential polynomial index", "s * (c[4] / 5.0 + s * c[5] / 6.0)", "s * (c[4] / 5.0 + s * c[5] / 5.0)"),

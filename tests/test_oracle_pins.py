@@ -376,13 +376,16 @@ def test_binning_invariants_and_numpy_restatement():
     cid = (cells[2] * n + cells[1]) * n + cells[0]
     assert np.array_equal(cid, b["cell_of"])
     for k, (cc, xw) in enumerate(zip(cells, wr)):
-        o = (xw - cc.astype(np.float32) * w).astype(np.float32)
+        ctr = ((cc.astype(np.float32) + np.float32(0.5)) * w).astype(np.float32)  # the cell centre
+        o = (xw - ctr).astype(np.float32)
         assert np.array_equal(s4[:, k].view(np.int32), o[perm].view(np.int32))
     assert np.array_equal(s4[:, 3], m[perm])
-    # offsets lie in the cell (to float32 rounding) and reproduce the position mod L
-    assert np.all(s4[:, :3] > -1e-5) and np.all(s4[:, :3] < w + 1e-5)
+    # offsets lie in the cell, [-w/2, w/2] about its centre (to float32 rounding),
+    # and reproduce the position mod L
+    assert np.all(s4[:, :3] > -0.5 * w - 1e-5) and np.all(s4[:, :3] < 0.5 * w + 1e-5)
+    assert np.max(np.abs(s4[:, :3])) > 0.45 * w
     ccell = b["cell_of"][perm]
-    org = np.stack([ccell % n, (ccell // n) % n, ccell // (n * n)], 1) * np.float64(w)
+    org = (np.stack([ccell % n, (ccell // n) % n, ccell // (n * n)], 1) + 0.5) * np.float64(w)
     pos = np.stack([x, y, z], 1)[perm].astype(np.float64)
     diff = s4[:, :3].astype(np.float64) + org - pos
     diff -= np.float64(L) * np.round(diff / np.float64(L))
@@ -390,7 +393,7 @@ def test_binning_invariants_and_numpy_restatement():
 
 
 def test_binning_with_displacements_keeps_float64_positions():
-    """Displacement mode: the offset plus the cell origin reproduces the float64
+    """Displacement mode: the offset plus the cell centre reproduces the float64
     position x + d (mod L) to float32 precision of the offset (not of L), and
     the steps restate bit for bit in numpy float64."""
     rng = np.random.default_rng(32)
@@ -413,11 +416,11 @@ def test_binning_with_displacements_keeps_float64_positions():
         pw = np.where(pw < 0, pw + np.float64(L), pw)
         pw = np.where(pw >= np.float64(L), pw - np.float64(L), pw)
         c = np.clip(np.floor(pw * np.float64(iw)).astype(np.int64), 0, n - 1)
-        cw = (c.astype(np.float32) * w).astype(np.float32)
-        o = (pw - cw.astype(np.float64)).astype(np.float32)
+        ctr = ((c.astype(np.float32) + np.float32(0.5)) * w).astype(np.float32)
+        o = (pw - ctr.astype(np.float64)).astype(np.float32)
         assert np.array_equal(s4[:, k].view(np.int32), o[perm].view(np.int32))
-        err = (o.astype(np.float64) + cw - pw)
-        assert np.max(np.abs(err)) <= 4.0 * np.spacing(np.float32(2 * w))
+        err = (o.astype(np.float64) + ctr - pw)
+        assert np.max(np.abs(err)) <= 0.5 * np.spacing(np.float32(0.5 * w))
     cid = b["cell_of"]
     assert np.all(np.diff(cid[perm]) >= 0)
 

@@ -57,6 +57,9 @@ extern "C" {
 #define HACC_STATUS_TIMEOUT 2u  /* a bounded device wait gave up; results invalid */
 #define HACC_STATUS_NONFINITE 4u /* a position was NaN or infinite (binned to 0) */
 #define HACC_STATUS_SKIN 8u      /* a drifted offset left its cell widened by skin/2: re-bin */
+#define HACC_STATUS_BOUNDS 16u   /* debug build only (libhacc_sr_debug.so, compiled with
+                                    HACC_DEBUG_BOUNDS): an index read from the lists, tasks or
+                                    binning was out of range; the work it led to was skipped */
 
 /* One periodic volume of the chaining mesh (64 bytes).  Filled on the host by
  * hacc_mesh_plan, then copied by the caller to device memory. */

@@ -21,6 +21,7 @@ HACC_STATUS_CAPACITY = 1
 HACC_STATUS_TIMEOUT = 2
 HACC_STATUS_NONFINITE = 4
 HACC_STATUS_SKIN = 8
+HACC_STATUS_BOUNDS = 16
 
 _ERRNAMES = {HACC_ERR_INVALID: "invalid argument", HACC_ERR_CAPACITY: "buffer or workspace too small",
              HACC_ERR_CUDA: "CUDA error", HACC_ERR_TIMEOUT: "timeout"}
@@ -124,22 +125,41 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _open(path: str):
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def load(build_if_missing: bool = True):
     """Load libhacc_sr.so (building it first if needed); raises if impossible."""
     global _lib
     with _lock:
         if _lib is None:
             if build_if_missing and not _build.up_to_date():
-                _build.build()
+                _build.build(variants=("release",))
             if not os.path.exists(_build.LIB):
                 raise HaccError(f"CUDA library missing: {_build.LIB} (run __graft_entry__.build())")
-            lib = ctypes.CDLL(_build.LIB)
-            for name, (res, args) in SIGNATURES.items():
-                fn = getattr(lib, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = lib
+            _lib = _open(_build.LIB)
     return _lib
+
+
+def use_library(debug: bool):
+    """Route every later call through the debug build (bounds-checked pair
+    kernels, libhacc_sr_debug.so) or back to the product build; returns the
+    previously active library handle.  Device buffers are shared: both
+    libraries run in the process's one CUDA context."""
+    global _lib
+    prev = load()
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if debug and not _build.up_to_date("debug"):
+        _build.build(variants=("debug",))
+    with _lock:
+        _lib = _open(path)
+    return prev
 
 
 def check(rc: int, what: str) -> None:

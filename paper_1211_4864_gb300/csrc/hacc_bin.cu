@@ -165,7 +165,7 @@ k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *
 // whatever the atomics gave; k_bin_order restores ascending index order.
 __global__ void __launch_bounds__(KEY_THREADS)
 k_bin_slots(int64_t N, const int32_t *__restrict__ cell_of, int32_t *__restrict__ cursor,
-            int32_t *__restrict__ unsorted)
+            int32_t *__restrict__ unsorted, uint32_t *status)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * PPL;
@@ -190,6 +190,12 @@ k_bin_slots(int64_t N, const int32_t *__restrict__ cell_of, int32_t *__restrict_
         for (int k = 0; k < PPL; ++k) {
             const int32_t b = __shfl_sync(FULL_MASK, base[k], run[k].start);
             const int64_t i = i0 + lane + 32 * k;
+#ifdef HACC_DEBUG_BOUNDS
+            if (i < N && (b + run[k].rank < 0 || b + run[k].rank >= N)) {
+                atomicOr(status, HACC_STATUS_BOUNDS);
+                continue;
+            }
+#endif
             if (i < N) unsorted[b + run[k].rank] = (int32_t)i;
         }
     }
@@ -780,7 +786,8 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     if (rc) return rc;
     // the counts are spent: their array becomes the per-cell cursor
     HACC_CUDA_TRY(cudaMemcpyAsync(b.cnt, out->cell_start, (size_t)nc * 4, cudaMemcpyDeviceToDevice, st));
-    k_bin_slots<<<grid_for((N + PPL - 1) / PPL, KEY_THREADS), KEY_THREADS, 0, st>>>(N, out->cell_of, b.cnt, b.unsorted);
+    k_bin_slots<<<grid_for((N + PPL - 1) / PPL, KEY_THREADS), KEY_THREADS, 0, st>>>(N, out->cell_of, b.cnt, b.unsorted,
+                                                                                      status);
     HACC_LAUNCH_CHECK();
     float4 *s4 = reinterpret_cast<float4 *>(out->sorted4);
     k_bin_order<<<grid_for((nc + 31) / 32 * 32, ORDER_THREADS), ORDER_THREADS, 0, st>>>(

@@ -471,13 +471,14 @@ __global__ void __launch_bounds__(256, min_ctas(MODE)) k_pairs(const KArgs a)
     }
     __syncwarp();
 
-    const int ntask = *a.n_tasks;
+    const int ntask = task_count(a);
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntask) break;
-        const int4 task = a.tasks[a.order[t]];
+        int4 task;
+        if (!take_task(a, t, lane, task, a.order)) continue;
         const hacc_volume &vol = a.vols[task.w];
         bool ok = true;
         // sub-chunks of larger tasks: 128 particles (four i per lane) for the adjoint's W form,
@@ -510,10 +511,11 @@ k_count_pairs(const KArgs a, unsigned long long *__restrict__ total)
 {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    const int ntask = *a.n_tasks;
+    const int ntask = task_count(a);
     unsigned long long cnt = 0;
     for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntask; t += warps) {
-        const int4 task = a.tasks[t];
+        int4 task;
+        if (!take_task(a, t, lane, task, nullptr)) continue;
         const hacc_volume &vol = a.vols[task.w];
         const int n = vol.n;
         const float w = vol.w;

@@ -49,6 +49,9 @@ struct KArgs {
     PairConsts k;
     const uint32_t *mass_varies;  // 0: every mass equal (the equal-mass force paths); NULL: general
     long long wait_limit;         // bound of each tile wait, clock64 cycles
+    // sizes the debug build's bounds checks compare indices with
+    int64_t N, n_cells, n_entries, task_cap;
+    int V;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -102,6 +105,70 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long lo
         const uint32_t ok = mbar_try_wait(bar, parity);
         if (__all_sync(FULL, ok)) return true;
     }
+}
+
+// The number of tasks to run, and task t of the heaviest-first order, with
+// whether it may be run.  A product build just reads them.  A debug build
+// (HACC_DEBUG_BOUNDS) first checks every index the task leads to -- the task
+// count against the task buffer, its order entry and record, its volume, and
+// on a chaining mesh its cell, its slot range and each entry of the cell's
+// neighbour list with the slot range that entry names -- and skips a task
+// that fails with HACC_STATUS_BOUNDS set, so that corrupted lists or tasks
+// never turn into out-of-range accesses.  (Tree lists are checked up to the
+// volume: the leaf count lives on the device.)  Warp-uniform.
+__device__ __forceinline__ int task_count(const KArgs &a)
+{
+    const int nt = *a.n_tasks;
+#ifdef HACC_DEBUG_BOUNDS
+    if (nt < 0 || nt > a.task_cap) {
+        if ((threadIdx.x & 31) == 0) atomicOr(a.status, HACC_STATUS_BOUNDS);
+        return nt < 0 ? 0 : (int)a.task_cap;
+    }
+#endif
+    return nt;
+}
+
+__device__ __forceinline__ bool take_task(const KArgs &a, int t, int lane, int4 &task, const int32_t *order)
+{
+#ifndef HACC_DEBUG_BOUNDS
+    task = a.tasks[order ? order[t] : t];
+    return true;
+#else
+    const int oi = order ? order[t] : t;
+    bool ok = oi >= 0 && oi < a.task_cap;
+    task = ok ? a.tasks[oi] : make_int4(0, 0, 0, 0);
+    ok = ok && task.w >= 0 && task.w < a.V;
+    if (ok && !a.origin) {
+        const hacc_volume &vol = a.vols[task.w];
+        const int64_t cb = vol.cell_base, ce = vol.cell_base + (int64_t)vol.n * vol.n * vol.n;
+        ok = task.x >= cb && task.x < ce && ce <= a.n_cells;
+        if (ok) {
+            const int s0 = a.cell_start[task.x], s1 = a.cell_start[task.x + 1];
+            ok = 0 <= s0 && s0 <= task.y && task.y < task.z && task.z <= s1 && s1 <= a.N;
+        }
+        if (ok) {
+            const int64_t e0 = a.nbr_off[task.x], e1 = a.nbr_off[task.x + 1];
+            ok = e0 >= 0 && e1 == e0 + vol.S && e1 <= a.n_entries;
+            if (ok) {
+                bool lane_ok = true;
+                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                    const int cp = a.nbr_cell[e];
+                    const int sh = a.nbr_shift[e];
+                    bool eok = cp >= cb && cp < ce && sh >= 0 && sh < 27;
+                    if (eok) {
+                        const int j0 = a.cell_start[cp], j1 = a.cell_start[cp + 1];
+                        eok = 0 <= j0 && j0 <= j1 && j1 <= a.N;
+                    }
+                    lane_ok = lane_ok && eok;
+                }
+                ok = __all_sync(FULL, lane_ok);
+            }
+        }
+    }
+    ok = __all_sync(FULL, ok);
+    if (!ok && lane == 0) atomicOr(a.status, HACC_STATUS_BOUNDS);
+    return ok;
+#endif
 }
 
 // s = a + b exactly as s + err (Knuth's TwoSum), err added to the low word.
@@ -370,6 +437,11 @@ KArgs base_args(const hacc_mesh *mesh, const hacc_binned *binned, const hacc_lis
     a.mass_varies = binned->mass_varies;
     a.status = status;
     a.wait_limit = WAIT_LIMIT_CYCLES;
+    a.N = mesh->N;
+    a.n_cells = mesh->n_cells;
+    a.n_entries = mesh->n_entries;
+    a.task_cap = lists->task_cap;
+    a.V = mesh->V;
     pair_consts(p, a.k);
     return a;
 }

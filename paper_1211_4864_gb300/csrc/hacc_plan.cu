@@ -4,7 +4,11 @@
 
 #include "hacc_common.cuh"
 
+#ifdef HACC_DEBUG_BOUNDS
+extern "C" const char *hacc_version(void) { return "hacc_sr 1 sm_103a debug-bounds"; }
+#else
 extern "C" const char *hacc_version(void) { return "hacc_sr 1 sm_103a"; }
+#endif
 
 extern "C" int hacc_get_status(const uint32_t *status, uint32_t *value, void *stream)
 {

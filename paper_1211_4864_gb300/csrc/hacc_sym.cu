@@ -413,13 +413,14 @@ __global__ void __launch_bounds__(256, 3) k_pairs_sym(const KArgs a, double *acc
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncwarp();
-    const int ntask = *a.n_tasks;
+    const int ntask = task_count(a);
     while (true) {
         int t = 0;
         if (lane == 0) t = atomicAdd(a.counter, 1);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntask) break;
-        const int4 task = a.tasks[a.order[t]];
+        int4 task;
+        if (!take_task(a, t, lane, task, a.order)) continue;
         const hacc_volume &vol = a.vols[task.w];
         bool ok;
         const int size = task.z - task.y;

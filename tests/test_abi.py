@@ -36,6 +36,19 @@ def test_header_symbols_exported(lib):
     assert set(_lib.SIGNATURES) == set(names)
 
 
+def test_debug_build_exports_the_same_symbols():
+    """libhacc_sr_debug.so (bounds-checked pair kernels) is built beside the
+    product library by __graft_entry__.build() and exports the same ABI."""
+    if not os.path.exists(_build.LIB_DEBUG):
+        pytest.skip("debug library not built")
+    dbg = ctypes.CDLL(_build.LIB_DEBUG)
+    for n in _header_functions():
+        assert hasattr(dbg, n), n
+    dbg.hacc_version.restype = ctypes.c_char_p
+    assert dbg.hacc_version().decode().endswith("debug-bounds")
+    assert os.path.dirname(_build.LIB_DEBUG) == os.path.dirname(_build.LIB)
+
+
 def test_library_is_in_tree_and_for_sm103a(lib):
     assert os.path.dirname(_build.LIB) == os.path.join(ROOT, "paper_1211_4864_gb300")
     assert "sm_103a" in lib.hacc_version().decode()

@@ -37,15 +37,16 @@ FLOPS_PER_PAIR_EQ = 28  # equal-mass path: no x m_j
 # subtract 1, x m_j and x m_i 2, both accumulations 12
 FLOPS_PER_SYM_PAIR = 36
 FLOPS_PER_SYM_PAIR_EQ = 34  # equal-mass path: no x m_j, x m_i
-# ncu DRAM bytes (read + write) per force launch on clustered256, per kernel, with the sources
-# they were taken from (null in the bench line once a source changes)
+# ncu DRAM bytes (read + write) of one force launch on clustered256 (dram__bytes_read.sum +
+# dram__bytes_write.sum, a capture of that kernel alone, -c 1), per kernel, with the sources they
+# were taken from (null in the bench line once a source changes)
 FORCE_TRAFFIC = {
-    "gather": {"workload": "clustered256", "bytes": 2216940416 + 964173632,
-               "sources": ["hacc_force.cu", "hacc_pairs.cuh"],
-               "sha256": "04360c7de1f51bd350abc5c81fffcae6239dea46664d8bcc33e87ec3fea8d6f4"},
-    "symmetric": {"workload": "clustered256", "bytes": 2794154598 + 1487683584,
-                  "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh"],
-                  "sha256": "fe7b6cdde8e806d03c4e4de705a650e3e954bb9031dd39b44a03bac755c2666f"},
+    "gather": {"workload": "clustered256", "bytes": 2215769856 + 965738240,
+               "sources": ["hacc_force.cu", "hacc_pairs.cuh", "hacc_common.cuh"],
+               "sha256": "f33c028c24cff617ab446f124bf0640bec48672f709b34739964367f8e5d7fe2"},
+    "symmetric": {"workload": "clustered256", "bytes": 2792809216 + 1489363968,
+                  "sources": ["hacc_sym.cu", "hacc_sym.cuh", "hacc_pairs.cuh", "hacc_common.cuh"],
+                  "sha256": "2f782f4823a30586354eecabd2d1f6a1934ce8370423d01b11480201df88b556"},
 }
 METRIC = "short-range pair interactions/s"
 UNIT = "pairs/s"
@@ -526,8 +527,9 @@ def binning_rate(torch, sr, pos, m, w, peaks, reps=5):
     return {"bin_ms": t_bin, "lists_ms": t_lists, "algorithmic_bytes": algo,
             "achieved_GBs": algo / (t_bin * 1e-3) / 1e9, "hbm_peak_GBs": hbm,
             "frac": algo / (t_bin * 1e-3) / 1e9 / hbm,
-            "note": "stable LSD radix sort (10-bit digits: two passes over a 20-bit cell key) plus the "
-                    "gather of the records; the sort's intermediate passes are not counted as algorithmic bytes"}
+            "note": "counting sort by cell: keys and counts, scan, atomic slots, per-cell index sort, record "
+                    "gather (random 16-byte reads); the slots and the sort's passes are not counted as "
+                    "algorithmic bytes"}
 
 
 def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, fpp_g, fpp_s, reps=3):

@@ -5,17 +5,18 @@
 // streaming hides memory latency.  The GPU analogue here streams the inputs
 // once and makes every later pass touch 4- or 16-byte words only:
 //   1. k_bin_keys: per particle its cell and packed (offset, mass) record in
-//      input order, and the cell counts (warp-aggregated atomics);
+//      input order, and the cell counts (one atomic per run of equal keys in
+//      a warp);
 //   2. an exclusive scan of the counts: cell_start;
 //   3. k_bin_slots: each particle takes a slot in its cell's range by an
 //      atomic cursor (the order inside a cell is then arbitrary);
 //   4. k_bin_order: each cell's input indices sorted ascending (the stable
-//      order, so the result does not depend on the atomics' order): one warp
-//      per cell of at most 32 particles (a bitonic network in registers) or
-//      at most 256 (in the warp's shared memory); larger cells go to
+//      order, so the result does not depend on the atomics' order): windows
+//      of small cells in one bitonic network in registers, cells of up to 256
+//      particles in a warp's shared memory; larger cells go to
 //      k_bin_order_big, one block per cell (LSD radix passes on the index
-//      digits).  The sorted indices are perm; the records are gathered into
-//      sorted4 in the same pass.
+//      digits).  The sorted indices are perm;
+//   5. k_bin_gather: the records gathered into sorted4 in perm's order.
 #include "hacc_common.cuh"
 
 namespace hacc {

@@ -212,3 +212,30 @@ def test_clustered256_rcb_tree_bit_exact_and_forces(clustered):
     ref = oracle.sr_force(w.x, w.y, w.z, w.m, float(w.L[0]), prm.eps, prm.rcut, prm.c.astype(np.float64), tg)
     rms, mx = err_norms(A[tg], ref)
     assert rms < RMS_TOL and mx < MAX_TOL, (rms, mx)
+
+
+def test_binning_bit_exact_beyond_2_26_particles():
+    """More than 2^26 particles: the binning's small-cell windows can no longer
+    pack (window cell, index) into one 32-bit key and sort one cell at a time
+    on the plain index; still bit-exact against the oracle (uniform particles,
+    about one per grid cell cubed)."""
+    torch = need_cuda()
+    import paper_1211_4864_gb300 as hs
+    hs.load()
+    N = (1 << 26) + 4099
+    L = np.float32(np.ceil(N ** (1.0 / 3.0)))
+    rng = np.random.default_rng(26)
+    x = (rng.random(N, dtype=np.float32) * L).astype(np.float32)
+    y = (rng.random(N, dtype=np.float32) * L).astype(np.float32)
+    z = (rng.random(N, dtype=np.float32) * L).astype(np.float32)
+    m = np.ones(N, np.float32)
+    sr = hs.ShortRange(np.array([L], np.float32), np.array([0, N], np.int64), 3.0)
+    sr.bin(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"), torch.tensor(z, device="cuda"),
+           torch.tensor(m, device="cuda"))
+    torch.cuda.synchronize()
+    sr.check_status()
+    ob = oracle.bin_volume(x, y, z, m, float(L), 3.0)
+    assert np.array_equal(sr.cell_of.cpu().numpy(), ob["cell_of"])
+    assert np.array_equal(sr.cell_start.cpu().numpy(), ob["cell_start"])
+    assert np.array_equal(sr.perm.cpu().numpy(), ob["perm"])
+    assert np.array_equal(sr.sorted4.cpu().numpy().view(np.int32), ob["sorted4"].view(np.int32))

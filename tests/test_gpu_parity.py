@@ -144,6 +144,28 @@ def test_bin_bit_exact_when_one_cell_holds_most_particles(torch, hs, N):
     assert int(np.diff(sr.cell_start.cpu().numpy()).max()) >= k
 
 
+def test_bin_bit_exact_at_every_sorting_path_boundary(torch, hs):
+    """Cell sizes on both sides of every boundary between the binning's
+    sorting paths (windows of small cells filling exactly 32 lanes or one
+    more, the warp's shared-memory network up to 256, the block radix passes
+    above), in a shuffled input order; bit-exact against the oracle."""
+    sizes = [0, 1, 2, 15, 16, 17, 31, 32, 33, 0, 63, 64, 65, 127, 128, 129, 255, 256, 257, 0, 511, 512, 513, 1,
+             1023, 1024, 1025]
+    rng = np.random.default_rng(77)
+    L = np.float32(9.0)  # 3 cells per side of width 3: 27 cells, one size each
+    parts = []
+    for c, k in enumerate(sizes):
+        cx, cy, cz = c % 3, (c // 3) % 3, c // 9
+        parts.append((rng.random((k, 3)) * 2.9 + 0.05 + 3.0 * np.array([cx, cy, cz])))
+    p = np.concatenate(parts)[rng.permutation(sum(sizes))].astype(np.float32)
+    N = p.shape[0]
+    w = Workload("boundaries", p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), np.ones(N, np.float32),
+                 np.zeros(N, np.float32), np.zeros(N, np.float32), np.zeros(N, np.float32),
+                 np.array([L], np.float32), np.array([0, N], np.int64))
+    sr = check_bin_lists(torch, hs, w, 3.0, 3.0, split_T=128)
+    assert sorted(np.diff(sr.cell_start.cpu().numpy()).tolist()) == sorted(sizes)
+
+
 def test_bin_lists_bit_exact_fine_mesh_and_edge_positions(torch, hs):
     """Cells narrower than r_c (reach 2: 125-cell stencils), coordinates on
     and outside the box edges, a ragged split size."""

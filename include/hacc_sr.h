@@ -196,7 +196,8 @@ size_t hacc_bin_workspace_size(const hacc_mesh *mesh);
  * keeps its float64 position to float32 precision of a cell-relative offset.
  * Within a cell the sorted order is ascending input index (bit-exact and
  * deterministic).  x, y, z, m: [N] input order.  Writes every array of `out`
- * (out->mass_varies if not NULL).
+ * (out->mass_varies if not NULL).  N and n_cells below 2^31, else
+ * HACC_ERR_INVALID.
  * A non-finite coordinate sets HACC_STATUS_NONFINITE and is binned as 0. */
 int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float *z,
              const float *dx, const float *dy, const float *dz, const float *m,
@@ -211,9 +212,9 @@ int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, const float 
  * library places in device memory when it is loaded: HACC_BIN_NOALLOC_BYTES
  * (9 MiB); every device that loads the library keeps it until the process
  * exits.  A problem fits when hacc_bin_workspace_size(mesh) is at most that,
- * about 20 bytes per particle plus 8 per cell (262,144 particles in up to
- * 500,000 cells); larger problems return HACC_ERR_CAPACITY (use hacc_bin with
- * a workspace).  The caller still passes the inputs and the outputs in `out`;
+ * about 30 bytes per particle whatever the number of cells (262,144
+ * particles fit, 400,000 do not); larger problems return HACC_ERR_CAPACITY
+ * (use hacc_bin with a workspace).  The caller still passes the inputs and the outputs in `out`;
  * nothing is allocated or freed, by this library or any other.
  * The first call on each device looks up the array's device address, with
  * that device current; make that first call before any stream capture (a

@@ -2,28 +2,33 @@
 //
 // The paper's tree build partitions structure-of-arrays particle data in three
 // phases (record, apply to six arrays, apply to the rest; Sec. III) so that
-// streaming hides memory latency.  The GPU analogue here streams the inputs
-// once and makes every later pass touch 4- or 16-byte words only:
-//   1. k_bin_keys: per particle its cell and packed (offset, mass) record in
-//      input order, and the cell counts (one atomic per run of equal keys in
-//      a warp);
-//   2. an exclusive scan of the counts: cell_start;
-//   3. k_bin_slots: each particle takes a slot in its cell's range by an
-//      atomic cursor (the order inside a cell is then arbitrary);
-//   4. k_bin_order: each cell's input indices sorted ascending (the stable
-//      order, so the result does not depend on the atomics' order): windows
-//      of small cells in one bitonic network in registers, cells of up to 256
-//      particles in a warp's shared memory; larger cells go to
-//      k_bin_order_big, one block per cell (LSD radix passes on the index
-//      digits).  The sorted indices are perm;
-//   5. k_bin_gather: the records gathered into sorted4 in perm's order.
+// streaming hides memory latency.  The GPU analogue here is a
+// least-significant-digit counting sort on the cell key that carries each
+// particle's record through its passes, so that every pass reads its input
+// in order and writes its output in runs of consecutive slots (no atomics
+// on global memory, no random gathers):
+//   1. k_bin_keys: per particle its cell key (cell_of, input order) and, per
+//      tile of BIN_TILE particles, the counts of the key's lowest 10-bit
+//      digit;
+//   2. an exclusive scan of those counts, digit-major: each tile's first
+//      slot for each digit;
+//   3. k_bin_scatter, once per digit from the lowest: each tile's particles
+//      ranked stably by the digit (warp match masks and per-warp counters, so
+//      equal digits keep the tile's order), staged in shared memory in digit
+//      order and stored to their slots -- key, input index and the
+//      (offset, mass) record (the first pass forms the record from the
+//      positions; later passes move it).  Before each later pass k_bin_hist
+//      counts the next digit per tile of the previous pass's output.  The
+//      last pass writes perm and sorted4 themselves;
+//   4. k_bin_cell_start: each cell's first slot by binary search of the
+//      sorted keys.
+// Each pass is stable, so within a cell the order is ascending input index.
 #include "hacc_common.cuh"
 
 namespace hacc {
 namespace {
 
-constexpr int KEY_THREADS = 256;
-constexpr int RADIX_BITS = 10;  // 1024 digits: a 20-bit cell key sorts in two passes
+constexpr int RADIX_BITS = 10;  // sort_index_stable: 1024 digits per pass
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int R_THREADS = 256;
 constexpr int R_WARPS = R_THREADS / 32;
@@ -81,437 +86,459 @@ __device__ __forceinline__ int axis_cell(float x, const float *d, int64_t i, con
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
-constexpr int PPL = 4;  // particles per lane in passes 1 and 2: lane l of a warp takes
-                        // particles i0 + l + 32 k, k < PPL (independent loads in flight)
+constexpr int BIN_BITS = 10;  // digit of one pass: a key below 2^20 sorts in two passes
+constexpr int BIN_DIGITS = 1 << BIN_BITS;
+constexpr int BIN_THREADS = 512;
+constexpr int BIN_ITEMS = 8;
+constexpr int BIN_TILE = BIN_THREADS * BIN_ITEMS;  // 4096 particles per tile
 
-// Runs of equal keys in consecutive lanes (the particles of a halo are often
-// consecutive): lane `start` of each run claims `len` values with one atomic,
-// lane start + r takes the r-th.  Every lane of the warp calls it; inactive
-// lanes (keys -1 - lane, unique) form runs of their own and claim nothing.
-struct Run {
-    int start, len, rank;
-};
+// k_bin_scatter: one block of SC_THREADS per SM, SC_ITEMS items per thread.
+constexpr int SC_THREADS = 1024;
+constexpr int SC_WARPS = SC_THREADS / 32;
+constexpr int SC_ITEMS = BIN_TILE / SC_THREADS;
+constexpr int SC_WORDS = BIN_DIGITS / 2 + 1;  // per-warp counters, two 16-bit digits a word; the
+                                              // last word takes the items past N
+// Its shared memory: the tile's inputs (copied in asynchronously; keys and
+// the tile's first global slot per digit double-buffered, one tile ahead),
+// the per-warp counters, the inverse of the tile's digit order, the tile's
+// first local slot per digit and the warp totals of the scan.
+constexpr size_t SM_REC = 0;
+constexpr size_t SM_IDX = SM_REC + sizeof(float4) * BIN_TILE;
+constexpr size_t SM_KEY = SM_IDX + sizeof(int32_t) * BIN_TILE;               // [2][BIN_TILE]
+constexpr size_t SM_BASE = SM_KEY + 2 * sizeof(int32_t) * BIN_TILE;          // [2][BIN_DIGITS]
+constexpr size_t SM_CNT = SM_BASE + 2 * sizeof(int32_t) * BIN_DIGITS;
+constexpr size_t SM_INV = SM_CNT + sizeof(uint32_t) * SC_WARPS * SC_WORDS;
+constexpr size_t SM_TSTART = SM_INV + sizeof(uint16_t) * BIN_TILE;
+constexpr size_t SM_WSUM = SM_TSTART + sizeof(int32_t) * BIN_DIGITS;
+constexpr size_t SCATTER_SMEM = SM_WSUM + sizeof(int32_t) * SC_WARPS;
+static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS == SC_THREADS && SC_WARPS % 2 == 0,
+              "one digit per thread in the scan, two digit words per thread in the prefix");
+static_assert(SCATTER_SMEM <= 227 * 1024, "shared memory of one block");
+static_assert(BIN_TILE <= 65536, "16-bit tile positions");
 
-__device__ __forceinline__ Run key_run(int32_t key)
+// Asynchronous copies of 4 and 16 bytes from global to shared memory
+// (cp.async), their commit and wait.
+__device__ __forceinline__ void async_copy4(void *dst, const void *src)
 {
-    const int lane = threadIdx.x & 31;
-    const int32_t prev = __shfl_up_sync(FULL_MASK, key, 1);
-    const unsigned starts = __ballot_sync(FULL_MASK, lane == 0 || prev != key);
-    const unsigned upto = (2u << lane) - 1u;  // lanes 0..lane
-    Run r;
-    r.start = 31 - __clz(starts & upto);
-    const unsigned after = starts & ~upto;
-    r.len = (after ? __ffs(after) - 1 : 32) - r.start;
-    r.rank = lane - r.start;
-    return r;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void async_copy16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
-// Pass 1: per particle, its cell key (cell_of) and its (offset, mass) record
-// in input order, and the count of each cell (cnt, cleared by the host;
-// one atomic per run of equal keys in a warp); with mass_varies, whether any mass
-// differs from the first particle's (N > 0).  Each warp walks runs of
-// 32 PPL consecutive particles, its lanes converged for the aggregation.
-__global__ void __launch_bounds__(KEY_THREADS)
-k_bin_keys(const hacc_volume *__restrict__ vols, int V, int64_t N, const float *__restrict__ x,
-           const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dx,
-           const float *__restrict__ dy, const float *__restrict__ dz, const float *__restrict__ m,
-           int32_t *__restrict__ cell_of, float4 *__restrict__ rec, int32_t *__restrict__ cnt,
-           uint32_t *status, uint32_t *mass_varies)
+// Asks the L2 to fetch [p, p + bytes) of global memory (a hint, no data
+// returned): whole 16-byte units from the first 16-byte boundary, in
+// pieces of at most 32 KB.  Called by one thread.
+__device__ __forceinline__ void prefetch_l2(const void *p, int64_t bytes)
 {
-    MassCheck mc(m, mass_varies);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    uintptr_t q = (a + 15) & ~(uintptr_t)15;
+    int64_t left = (bytes - (int64_t)(q - a)) & ~(int64_t)15;
+    while (left >= 16) {
+        const uint32_t n = left > 32768 ? 32768u : (uint32_t)left;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+        q += n;
+        left -= n;
+    }
+}
+
+// Elements [t BIN_TILE, (t + 1) BIN_TILE) of an array of N, clipped to N.
+template <class T>
+__device__ __forceinline__ void prefetch_tile(const T *a, int64_t t, int64_t N)
+{
+    const int64_t b = t * BIN_TILE;
+    if (a && b < N) prefetch_l2(a + b, (N - b < BIN_TILE ? N - b : BIN_TILE) * (int64_t)sizeof(T));
+}
+
+// The particle arrays of a binning call (dx, dy, dz all given or all NULL).
+struct ParticleIn {
+    const hacc_volume *vols;
+    int V;
+    const float *x, *y, *z, *dx, *dy, *dz, *m;
+};
+
+__device__ __forceinline__ int key_digit(int32_t key, int shift)
+{
+    return (int)(((uint32_t)key >> shift) & (BIN_DIGITS - 1));
+}
+
+// Adds one digit per thread to the tile's counters (BIN_DIGITS: no item):
+// a run of equal digits in consecutive lanes shares one shared-memory atomic.
+__device__ __forceinline__ void count_digit(int32_t *cnt, int d)
+{
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * PPL;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPL;
-    for (int64_t i0 = warp0; i0 < N; i0 += stride) {
-        float px[PPL], py[PPL], pz[PPL], pm[PPL];
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int64_t i = i0 + lane + 32 * k;
-            const bool ok = i < N;
-            px[k] = ok ? x[i] : 0.f;
-            py[k] = ok ? y[i] : 0.f;
-            pz[k] = ok ? z[i] : 0.f;
-            pm[k] = ok ? m[i] : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int64_t i = i0 + lane + 32 * k;
-            const bool active = i < N;
-            int32_t key = 0;
-            if (active) {
-                const int v = find_volume_by_particle(vols, V, i);
-                const hacc_volume &vol = vols[v];
-                const int n = vol.n;
-                float4 r;
-                const int cx = axis_cell(px[k], dx, i, vol, r.x, status);
-                const int cy = axis_cell(py[k], dy, i, vol, r.y, status);
-                const int cz = axis_cell(pz[k], dz, i, vol, r.z, status);
-                key = (int32_t)(vol.cell_base + ((int64_t)cz * n + cy) * n + cx);
-                cell_of[i] = key;
-                r.w = pm[k];
-                __stcs(&rec[i], r);
-                mc.check(r.w);
+    const int prev = __shfl_up_sync(FULL_MASK, d, 1);
+    const unsigned starts = __ballot_sync(FULL_MASK, lane == 0 || prev != d);
+    if (d < BIN_DIGITS && ((starts >> lane) & 1u)) {
+        const unsigned after = starts & ~((2u << lane) - 1u);
+        atomicAdd(&cnt[d], (after ? __ffs(after) - 1 : 32) - lane);
+    }
+}
+
+// Pass 1: per particle its cell key (cell_of) and its (offset, mass) record
+// (rec), both in input order; per tile (particles [t BIN_TILE, (t + 1)
+// BIN_TILE)) the counts of the key's lowest digit, digit-major into hist
+// (hist[t BIN_DIGITS + d], a row per tile); with mass_varies, whether any mass differs from the
+// first particle's (N > 0).  Persistent blocks take tiles in turn and ask
+// the L2 for their next tile's inputs while they work on the current one.
+// DISP: displacements are given (the float64 position path).
+template <bool DISP>
+__global__ void __launch_bounds__(BIN_THREADS, 2)
+k_bin_keys(ParticleIn P, int64_t N, int nblk, int32_t *__restrict__ cell_of, float4 *__restrict__ rec,
+           int32_t *__restrict__ hist, uint32_t *status, uint32_t *mass_varies)
+{
+    __shared__ int32_t cnt[BIN_DIGITS];
+    MassCheck mc(P.m, mass_varies);
+    for (int64_t t = blockIdx.x; t < nblk; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int64_t tn = t + gridDim.x;
+            prefetch_tile(P.x, tn, N);
+            prefetch_tile(P.y, tn, N);
+            prefetch_tile(P.z, tn, N);
+            prefetch_tile(P.m, tn, N);
+            if (DISP) {
+                prefetch_tile(P.dx, tn, N);
+                prefetch_tile(P.dy, tn, N);
+                prefetch_tile(P.dz, tn, N);
             }
-            const Run run = key_run(active ? key : -1 - lane);
-            if (active && run.rank == 0) atomicAdd(&cnt[key], run.len);
         }
+        for (int d = threadIdx.x; d < BIN_DIGITS; d += BIN_THREADS) cnt[d] = 0;
+        __syncthreads();
+        const int64_t t0 = t * BIN_TILE + threadIdx.x;
+        // items in groups of G, their loads in flight together (the float64
+        // path takes more registers)
+        constexpr int G = DISP ? 2 : 4;
+#pragma unroll
+        for (int g = 0; g < BIN_ITEMS; g += G) {
+            float px[G], py[G], pz[G], pm[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int64_t i = t0 + (int64_t)(g + k) * BIN_THREADS;
+                const bool ok = i < N;
+                px[k] = ok ? P.x[i] : 0.f;
+                py[k] = ok ? P.y[i] : 0.f;
+                pz[k] = ok ? P.z[i] : 0.f;
+                pm[k] = ok ? P.m[i] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int64_t i = t0 + (int64_t)(g + k) * BIN_THREADS;
+                int d = BIN_DIGITS;
+                if (i < N) {
+                    const hacc_volume &vol = P.vols[find_volume_by_particle(P.vols, P.V, i)];
+                    const int n = vol.n;
+                    float4 r;
+                    const int cx = axis_cell(px[k], DISP ? P.dx : nullptr, i, vol, r.x, status);
+                    const int cy = axis_cell(py[k], DISP ? P.dy : nullptr, i, vol, r.y, status);
+                    const int cz = axis_cell(pz[k], DISP ? P.dz : nullptr, i, vol, r.z, status);
+                    const int32_t key = (int32_t)(vol.cell_base + ((int64_t)cz * n + cy) * n + cx);
+                    r.w = pm[k];
+                    cell_of[i] = key;
+                    rec[i] = r;
+                    mc.check(pm[k]);
+                    d = key_digit(key, 0);
+                }
+                count_digit(cnt, d);
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < BIN_DIGITS; d += BIN_THREADS) hist[(int64_t)t * BIN_DIGITS + d] = cnt[d];
+        __syncthreads();
     }
     mc.finish();
 }
 
-// Pass 2: each particle takes a slot of its cell's range [cell_start[c],
-// cell_start[c + 1]) through the per-cell cursor (initialised to cell_start)
-// and leaves its input index there: a run of lanes with equal keys shares
-// one atomic and takes consecutive slots in lane order.  Within a cell the order is
-// whatever the atomics gave; k_bin_order restores ascending index order.
-__global__ void __launch_bounds__(KEY_THREADS)
-k_bin_slots(int64_t N, const int32_t *__restrict__ cell_of, int32_t *__restrict__ cursor,
-            int32_t *__restrict__ unsorted, uint32_t *status)
+// Before a later pass: the counts of the digit at `shift` per tile of the
+// previous pass's output keys, a row per tile (persistent blocks, next tile
+// prefetched as in k_bin_keys).
+__global__ void __launch_bounds__(BIN_THREADS)
+k_bin_hist(const int32_t *__restrict__ keys, int64_t N, int shift, int nblk, int32_t *__restrict__ hist)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * PPL;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPL;
-    for (int64_t i0 = warp0; i0 < N; i0 += stride) {
-        int32_t key[PPL], base[PPL];
-        Run run[PPL];
+    __shared__ int32_t cnt[BIN_DIGITS];
+    for (int64_t t = blockIdx.x; t < nblk; t += gridDim.x) {
+        if (threadIdx.x == 0) prefetch_tile(keys, t + gridDim.x, N);
+        for (int d = threadIdx.x; d < BIN_DIGITS; d += BIN_THREADS) cnt[d] = 0;
+        __syncthreads();
+        const int64_t t0 = t * BIN_TILE + threadIdx.x;
+        int32_t kk[BIN_ITEMS];
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int64_t i = i0 + lane + 32 * k;
-            key[k] = i < N ? __ldcs(&cell_of[i]) : -1 - lane;
+        for (int k = 0; k < BIN_ITEMS; ++k) {
+            const int64_t i = t0 + (int64_t)k * BIN_THREADS;
+            kk[k] = i < N ? keys[i] : 0;
         }
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) run[k] = key_run(key[k]);
-        // the atomics of the PPL rounds are independent: all in flight together
+        for (int k = 0; k < BIN_ITEMS; ++k)
+            count_digit(cnt, t0 + (int64_t)k * BIN_THREADS < N ? key_digit(kk[k], shift) : BIN_DIGITS);
+        __syncthreads();
+        for (int d = threadIdx.x; d < BIN_DIGITS; d += BIN_THREADS) hist[(int64_t)t * BIN_DIGITS + d] = cnt[d];
+        __syncthreads();
+    }
+}
+
+// One stable counting pass by the digit at `shift`.  Persistent blocks, one
+// per SM, take tiles in turn.  In tile t, warp w owns tile positions
+// [w 32 SC_ITEMS, (w + 1) 32 SC_ITEMS) and item k of lane l is position
+// w 32 SC_ITEMS + 32 k + l, so (warp, item, lane) order is input order and
+// equal digits keep it: an item's slot is the tile's first slot for its
+// digit (offs, the scanned counts) plus the number of earlier items of the
+// tile with that digit (per-warp counters).  Each thread copies its items'
+// key, index and record into shared memory asynchronously; the keys are
+// ranked while the rest lands.  The tile's items are then stored in digit
+// order (through the inverse of the ranking), so the stores to global memory
+// run along each digit's consecutive slots.  FIRST: the input is pass 1's
+// output (keys cell_of, records in input order; an item's index is its
+// position), otherwise the previous pass's (key, index, record) arrays.
+// N < 2^31.
+template <bool FIRST>
+__global__ void __launch_bounds__(SC_THREADS, 1)
+k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ idx_in,
+              const float4 *__restrict__ rec_in, int N, int shift, int nblk, const int32_t *__restrict__ offs,
+              int32_t *__restrict__ key_out, int32_t *__restrict__ idx_out, float4 *__restrict__ rec_out,
+              uint32_t *status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *srec = reinterpret_cast<float4 *>(smem + SM_REC);
+    int32_t *sidx = reinterpret_cast<int32_t *>(smem + SM_IDX);
+    int32_t *skey2 = reinterpret_cast<int32_t *>(smem + SM_KEY);
+    int32_t *base2 = reinterpret_cast<int32_t *>(smem + SM_BASE);
+    uint32_t(*wcnt)[SC_WORDS] = reinterpret_cast<uint32_t(*)[SC_WORDS]>(smem + SM_CNT);
+    uint16_t *inv = reinterpret_cast<uint16_t *>(smem + SM_INV);
+    int32_t *tstart = reinterpret_cast<int32_t *>(smem + SM_TSTART);
+    int32_t *wsum = reinterpret_cast<int32_t *>(smem + SM_WSUM);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int l0 = warp * (32 * SC_ITEMS) + lane;  // tile position of item 0
+    // a tile's keys and first global slots per digit, into buffer b
+    auto fetch_keys = [&](int t, int b) {
+        if (t < nblk) {
+            const int tile0 = t * BIN_TILE;
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            base[k] = 0;
-            if (i0 + lane + 32 * k < N && run[k].rank == 0) base[k] = atomicAdd(&cursor[key[k]], run[k].len);
+            for (int k = 0; k < SC_ITEMS; ++k)
+                if (tile0 + l0 + 32 * k < N)
+                    async_copy4(skey2 + b * BIN_TILE + l0 + 32 * k, key_in + tile0 + l0 + 32 * k);
+            async_copy4(base2 + b * BIN_DIGITS + threadIdx.x, offs + (int64_t)t * BIN_DIGITS + threadIdx.x);
         }
+        async_commit();
+    };
+    fetch_keys(blockIdx.x, 0);
+    int buf = 0;
+    for (int t = blockIdx.x; t < nblk; t += gridDim.x, buf ^= 1) {
+        const int tile0 = t * BIN_TILE;
+        const int32_t *skey = skey2 + buf * BIN_TILE;
+        const int32_t *base_d = base2 + buf * BIN_DIGITS;
+        async_wait<0>();  // this tile's keys and slots (fetched during the previous tile)
+        for (int i = threadIdx.x; i < SC_WARPS * SC_WORDS; i += SC_THREADS) (&wcnt[0][0])[i] = 0u;
+        __syncthreads();
+        // the tile's indices and records land while its keys are ranked; the
+        // next tile's keys and slots while this one is stored
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) {
-            const int32_t b = __shfl_sync(FULL_MASK, base[k], run[k].start);
-            const int64_t i = i0 + lane + 32 * k;
+        for (int k = 0; k < SC_ITEMS; ++k) {
+            const int l = l0 + 32 * k;
+            if (tile0 + l < N) {
+                if (!FIRST) async_copy4(sidx + l, idx_in + tile0 + l);
+                async_copy16(srec + l, rec_in + tile0 + l);
+            }
+        }
+        async_commit();
+        fetch_keys(t + gridDim.x, buf ^ 1);
+        if (threadIdx.x == 0) {
+            const int tn = t + 2 * gridDim.x;
+            prefetch_tile(key_in, tn, N);
+            prefetch_tile(rec_in, t + gridDim.x, N);
+            if (!FIRST) prefetch_tile(idx_in, t + gridDim.x, N);
+        }
+        int32_t key[SC_ITEMS];
+        int slot[SC_ITEMS];
+        // rank of each item among the warp's earlier items with its digit:
+        // the lowest lane of each group of equal digits adds the group to the
+        // warp's counter and hands the old count to the group
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k) {
+            const bool ok = tile0 + l0 + 32 * k < N;
+            key[k] = ok ? skey[l0 + 32 * k] : 0;
+            const int d = ok ? key_digit(key[k], shift) : BIN_DIGITS;
+            const unsigned peers = __match_any_sync(FULL_MASK, d);
+            const int leader = __ffs(peers) - 1;
+            const int half = (d & 1) * 16;
+            uint32_t old = 0u;
+            if (lane == leader) old = atomicAdd(&wcnt[warp][d >> 1], (uint32_t)__popc(peers) << half);
+            old = __shfl_sync(FULL_MASK, old, leader);
+            slot[k] = (int)((old >> half) & 0xffffu) + __popc(peers & lt);
+        }
+        __syncthreads();
+        // per digit pair: exclusive prefix over the warps (both halves at
+        // once: a tile's count per digit stays below 2^16), and the tile's
+        // count per digit
+        // (thread j + 512 h takes warps [16 h, 16 h + 16) of word j; the
+        // upper half then adds the lower half's total)
+        {
+            constexpr int HW = SC_WARPS / 2;
+            const int j = threadIdx.x & (BIN_DIGITS / 2 - 1), h = threadIdx.x / (BIN_DIGITS / 2);
+            uint32_t run = 0u;
+#pragma unroll
+            for (int w = h * HW; w < (h + 1) * HW; ++w) {
+                const uint32_t c = wcnt[w][j];
+                wcnt[w][j] = run;
+                run += c;
+            }
+            if (h == 0) tstart[2 * j] = (int)run;  // the lower half's packed total, for the upper half
+            __syncthreads();
+            if (h == 1) {
+                const uint32_t lower = (uint32_t)tstart[2 * j];
+#pragma unroll
+                for (int w = HW; w < SC_WARPS; ++w) wcnt[w][j] += lower;
+                run += lower;
+                tstart[2 * j] = (int)(run & 0xffffu);
+                tstart[2 * j + 1] = (int)(run >> 16);
+            }
+        }
+        __syncthreads();
+        // exclusive scan of the tile's digit counts (one per thread): its
+        // first local slot per digit
+        {
+            const int v = tstart[threadIdx.x];
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(FULL_MASK, inc, o);
+                if (lane >= o) inc += n;
+            }
+            if (lane == 31) wsum[warp] = inc;
+            __syncthreads();
+            int before = lane < warp ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL_MASK, before, o);
+            tstart[threadIdx.x] = before + inc - v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k) {
+            if (tile0 + l0 + 32 * k < N) {
+                const int d = key_digit(key[k], shift);
+                inv[slot[k] + tstart[d] + (int)((wcnt[warp][d >> 1] >> ((d & 1) * 16)) & 0xffffu)] =
+                    (uint16_t)(l0 + 32 * k);
+            }
+        }
+        async_wait<1>();  // this tile's indices and records (the next tile's keys may still be in flight)
+        __syncthreads();
+        const int nv = N - tile0 < BIN_TILE ? N - tile0 : BIN_TILE;
+        for (int j = threadIdx.x; j < nv; j += SC_THREADS) {
+            const int l = inv[j];
+            const int32_t kk = skey[l];
+            const int d = key_digit(kk, shift);
+            const int pos = base_d[d] + (j - tstart[d]);
 #ifdef HACC_DEBUG_BOUNDS
-            if (i < N && (b + run[k].rank < 0 || b + run[k].rank >= N)) {
+            if (pos < 0 || pos >= N) {
                 atomicOr(status, HACC_STATUS_BOUNDS);
                 continue;
             }
 #endif
-            if (i < N) unsorted[b + run[k].rank] = (int32_t)i;
+            key_out[pos] = kk;
+            idx_out[pos] = FIRST ? tile0 + l : sidx[l];
+            rec_out[pos] = srec[l];
         }
+        __syncthreads();  // shared memory is reused by the next tile
     }
+    async_wait<0>();
 }
 
-// Ascending bitonic sort of one value per lane over the first P lanes
-// (P a power of two, 2..32, fixed at compile time so the network unrolls):
-// lanes below P end up in ascending order.
-template <int P>
-__device__ __forceinline__ int32_t warp_bitonic_n(int32_t v)
+constexpr int SCAN_TC = 32;  // tiles per chunk of the digit-count scan
+
+// Scan of the per-tile digit counts into each tile's first slot per digit,
+// offs[t][d] = (count of digits below d) + (count of digit d in tiles before
+// t); rows of BIN_DIGITS per tile.  Step 1: per chunk of SCAN_TC tiles, the
+// sum of each digit's counts.
+__global__ void __launch_bounds__(BIN_DIGITS)
+k_bin_scan_chunks(const int32_t *__restrict__ hist, int nblk, int32_t *__restrict__ csum)
+{
+    const int c = blockIdx.x, d = threadIdx.x;
+    const int t1 = min(nblk, (c + 1) * SCAN_TC);
+    int s = 0;
+#pragma unroll 8
+    for (int t = c * SCAN_TC; t < t1; ++t) s += hist[(int64_t)t * BIN_DIGITS + d];
+    csum[(int64_t)c * BIN_DIGITS + d] = s;
+}
+
+// Step 2: per digit (one warp each, its lanes over the chunks), the
+// exclusive prefix of its chunk sums in place, and its total.
+__global__ void __launch_bounds__(BIN_DIGITS)
+k_bin_scan_digits(int32_t *__restrict__ csum, int nchunks, int32_t *__restrict__ total)
 {
     const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= P; k <<= 1)
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int32_t o = __shfl_xor_sync(FULL_MASK, v, j);
-            const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
-            v = keep_min ? min(v, o) : max(v, o);
-        }
-    return v;
-}
-
-// The same for any count n <= 32 of valid lanes (the others hold INT32_MAX).
-__device__ __forceinline__ int32_t warp_bitonic(int32_t v, int n)
-{
-    if (n <= 1) return v;
-    if (n <= 2) return warp_bitonic_n<2>(v);
-    if (n <= 4) return warp_bitonic_n<4>(v);
-    if (n <= 8) return warp_bitonic_n<8>(v);
-    if (n <= 16) return warp_bitonic_n<16>(v);
-    return warp_bitonic_n<32>(v);
-}
-
-constexpr int ORDER_THREADS = 256;
-constexpr int ORDER_WARPS = ORDER_THREADS / 32;
-constexpr int WARP_SORT_MAX = 256;  // cells up to this size are sorted by one warp
-
-constexpr int SEG_SHIFT = 26;  // packed sort key of a small-cell window: (segment << 26) | index
-
-// Pass 3: per cell, the input indices of its slots in ascending order
-// (perm).  A warp takes 32
-// consecutive cells at a time (their bounds one load per lane):
-//  * consecutive cells of at most 32 particles whose slots fit in 32 lanes
-//    form a window sorted at once: one slot per lane, key (segment, index)
-//    where the segment is the lane's cell within the window, so a single
-//    bitonic network sorts every cell of the window (indices below 2^26; for
-//    larger N a window holds one cell and the key is the index);
-//  * a cell of up to WARP_SORT_MAX particles: the warp's shared memory
-//    (bitonic network, padded with INT32_MAX);
-//  * larger cells: appended to big_list for k_bin_order_big.
-// The next window's slots are loaded while the current one is sorted.  The
-// records follow in k_bin_gather (and k_bin_order_big).
-__global__ void __launch_bounds__(ORDER_THREADS)
-k_bin_order(int64_t n_cells, const int32_t *__restrict__ cell_start, const int32_t *__restrict__ unsorted,
-            int32_t *__restrict__ perm, int32_t *__restrict__ big_list, int32_t *__restrict__ big_count,
-            int packed)
-{
-    __shared__ int32_t buf[ORDER_WARPS][WARP_SORT_MAX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t *sb = buf[warp];
-    const int64_t warps = (int64_t)gridDim.x * ORDER_WARPS;
-    for (int64_t c0 = ((int64_t)blockIdx.x * ORDER_WARPS + warp) * 32; c0 < n_cells; c0 += warps * 32) {
-        const int nc = (int)min((int64_t)32, n_cells - c0);
-        const int64_t cl = c0 + min(lane, nc - 1);
-        const int32_t lo = lane < nc ? cell_start[cl] : cell_start[cl + 1];  // lanes past the group: empty cells
-        const int32_t hi = cell_start[cl + 1];
-        const int32_t gend = __shfl_sync(FULL_MASK, hi, 31);
-
-        // slots from b on, speculatively 32 of them (a window never holds more)
-        auto slots_from = [&](int32_t b) { return b + lane < gend ? unsorted[b + lane] : INT32_MAX; };
-        int q = 0;
-        int32_t next = slots_from(__shfl_sync(FULL_MASK, lo, 0));  // from the group's first slot
-        while (q < nc) {
-            const int32_t b = __shfl_sync(FULL_MASK, lo, q);
-            const int32_t n = __shfl_sync(FULL_MASK, hi, q) - b;
-            if (n == 0) {
-                ++q;
-                continue;
-            }
-            if (n <= 32) {
-                // the window: cells q..ql whose slots end within b + 32 (hi is non-decreasing)
-                const unsigned fit = __ballot_sync(FULL_MASK, lane >= q && lane < nc && hi - b <= 32);
-                const int ql = packed ? 31 - __clz(fit) : q;
-                const int32_t W = __shfl_sync(FULL_MASK, hi, ql) - b;
-                // segment of each slot: boundaries at the first slots of cells q..ql
-                const unsigned bit = (lane >= q && lane <= ql && lo - b < 32) ? 1u << (lo - b) : 0u;
-                const unsigned bounds = __reduce_or_sync(FULL_MASK, bit);
-                const int seg = __popc(bounds & ((2u << lane) - 1u)) - 1;
-                const int32_t v = next;
-                if (ql + 1 < nc) next = slots_from(__shfl_sync(FULL_MASK, lo, ql + 1));
-                int32_t key = lane < W ? (packed ? (seg << SEG_SHIFT) | v : v) : INT32_MAX;
-                key = warp_bitonic(key, W);
-                if (lane < W) perm[b + lane] = packed ? key & ((1 << SEG_SHIFT) - 1) : key;
-                q = ql + 1;
-                continue;
-            }
-            if (q + 1 < nc) next = slots_from(__shfl_sync(FULL_MASK, lo, q + 1));
-            if (n <= WARP_SORT_MAX) {
-                int P = 64;
-                while (P < n) P <<= 1;
-                for (int t = lane; t < P; t += 32) sb[t] = t < n ? unsorted[b + t] : INT32_MAX;
-                __syncwarp();
-                for (int k = 2; k <= P; k <<= 1)
-                    for (int j = k >> 1; j > 0; j >>= 1) {
-                        for (int t = lane; t < P / 2; t += 32) {
-                            const int e = 2 * t - (t & (j - 1));  // element whose bit j is clear
-                            const int32_t u = sb[e], w = sb[e + j];
-                            const bool asc = (e & k) == 0;
-                            if ((u > w) == asc) {
-                                sb[e] = w;
-                                sb[e + j] = u;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                for (int t = lane; t < n; t += 32) perm[b + t] = sb[t];
-                __syncwarp();
-            } else if (lane == 0) {
-                big_list[atomicAdd(big_count, 1)] = (int32_t)(c0 + q);
-            }
-            ++q;
-        }
-    }
-}
-
-// A 16-byte load from a random place: the L2 fetches only the 64-byte block
-// that holds it, not a longer neighbourhood.
-__device__ __forceinline__ float4 load_random16(const float4 *p)
-{
-    float4 r;
-    asm volatile("ld.global.L2::64B.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "l"(p));
-    return r;
-}
-
-// Pass 4: the records in sorted order, sorted4[k] = rec[perm[k]]; each lane
-// gathers PPL records with all loads in flight together.
-__global__ void __launch_bounds__(KEY_THREADS)
-k_bin_gather(int64_t N, const int32_t *__restrict__ perm, const float4 *__restrict__ rec,
-             float4 *__restrict__ sorted4)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * PPL;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPL;
-    for (int64_t k0 = warp0; k0 < N; k0 += stride) {
-        int32_t src[PPL];
-        float4 r[PPL];
-#pragma unroll
-        for (int u = 0; u < PPL; ++u) {
-            const int64_t k = k0 + lane + 32 * u;
-            src[u] = k < N ? perm[k] : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < PPL; ++u)
-            if (k0 + lane + 32 * u < N) r[u] = load_random16(&rec[src[u]]);
-#pragma unroll
-        for (int u = 0; u < PPL; ++u) {
-            const int64_t k = k0 + lane + 32 * u;
-            if (k < N) sorted4[k] = r[u];
-        }
-    }
-}
-
-constexpr int BIG_THREADS = 512;
-constexpr int BIG_WARPS = BIG_THREADS / 32;
-constexpr int DIGIT_BITS = 8;
-constexpr int DIGITS = 1 << DIGIT_BITS;
-
-// Lanes (among the valid ones) whose digit equals this lane's: one ballot per
-// digit bit.
-__device__ __forceinline__ unsigned same_digit_lanes(int d, bool ok)
-{
-    unsigned eq = __ballot_sync(FULL_MASK, ok);
-#pragma unroll
-    for (int b = 0; b < DIGIT_BITS; ++b) {
-        const bool bit = (d >> b) & 1;
-        const unsigned bal = __ballot_sync(FULL_MASK, bit);
-        eq &= bit ? bal : ~bal;
-    }
-    return eq;
-}
-
-// Index digit at `shift` (0 beyond the 32 bits: such a pass is a stable copy).
-__device__ __forceinline__ int index_digit(int32_t v, int shift)
-{
-    return shift < 32 ? (int)(((uint32_t)v >> shift) & (DIGITS - 1)) : 0;
-}
-
-constexpr int IPT = 16;  // indices per lane per round of a counting pass
-
-// One stable counting pass of a block over n indices by the digit at
-// `shift`: src -> dst (global memory, the cell's own ranges of the two
-// buffers).  Warp w owns items [w chunk, (w + 1) chunk) and walks them in
-// rounds of 32 IPT, lane l taking items r + 32 k + l (all IPT loads issued
-// before any is used), so (warp, round, k, lane) order is item order; ranks
-// among equal digits come from lane masks (one ballot per digit bit) and
-// per-warp counters, computed once to count and again to place.
-__device__ void block_digit_pass(const int32_t *src, int32_t *dst, int n, int shift, int32_t (*wcnt)[DIGITS],
-                                 int32_t *dtot)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < BIG_WARPS * DIGITS; t += BIG_THREADS) (&wcnt[0][0])[t] = 0;
-    __syncthreads();
-    constexpr int ROUND = 32 * IPT;
-    const int chunk = (n + BIG_WARPS * 32 - 1) / (BIG_WARPS * 32) * 32;
-    const int beg = min(n, warp * chunk), end = min(n, beg + chunk);
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int r = beg; r < end; r += ROUND) {
-        int32_t v[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const int it = r + 32 * k + lane;
-            v[k] = it < end ? src[it] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            if (r + 32 * k >= end) break;  // warp-uniform
-            const bool ok = r + 32 * k + lane < end;
-            const int d = ok ? index_digit(v[k], shift) : DIGITS;
-            const unsigned peers = same_digit_lanes(d, ok);
-            if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // per digit: exclusive prefix over the warps, then over the digits
-    if (threadIdx.x < DIGITS) {
-        const int d = threadIdx.x;
-        int run = 0;
-        for (int w = 0; w < BIG_WARPS; ++w) {
-            const int c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
-        }
-        dtot[d] = run;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        constexpr int PER = DIGITS / 32;
-        int c[PER], sum = 0;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            c[q] = dtot[lane * PER + q];
-            sum += c[q];
-        }
-        int inc = sum;
+    const int d = blockIdx.x * (BIN_DIGITS / 32) + (threadIdx.x >> 5);
+    int carry = 0;
+    for (int c0 = 0; c0 < nchunks; c0 += 32) {
+        const int c = c0 + lane;
+        const int v = c < nchunks ? csum[(int64_t)c * BIN_DIGITS + d] : 0;
+        int inc = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(FULL_MASK, inc, o);
-            if (lane >= o) inc += t;
+            const int n = __shfl_up_sync(FULL_MASK, inc, o);
+            if (lane >= o) inc += n;
         }
-        int run = inc - sum;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            dtot[lane * PER + q] = run;
-            run += c[q];
-        }
+        if (c < nchunks) csum[(int64_t)c * BIN_DIGITS + d] = carry + inc - v;
+        carry += __shfl_sync(FULL_MASK, inc, 31);
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < BIG_WARPS * DIGITS; t += BIG_THREADS) (&wcnt[0][0])[t] += dtot[t % DIGITS];
-    __syncthreads();
-    for (int r = beg; r < end; r += ROUND) {
-        int32_t v[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            const int it = r + 32 * k + lane;
-            v[k] = it < end ? src[it] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            if (r + 32 * k >= end) break;  // warp-uniform
-            const bool ok = r + 32 * k + lane < end;
-            const int d = ok ? index_digit(v[k], shift) : DIGITS;
-            const unsigned peers = same_digit_lanes(d, ok);
-            int pos = 0;
-            if (ok) pos = wcnt[warp][d] + __popc(peers & lt);
-            __syncwarp();
-            if (ok && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-            __syncwarp();
-            if (ok) dst[pos] = v[k];
-        }
-    }
-    __syncthreads();
+    if (lane == 0) total[d] = carry;
 }
 
-// Pass 3 for the cells k_bin_order left (more than WARP_SORT_MAX particles):
-// one block per cell, taken in turn from big_list.  LSD radix passes of
-// DIGIT_BITS bits over the index bits, ping-ponging between the cell's range
-// of `unsorted` and of perm so that the last pass lands in perm (an odd
-// number of passes; a pass on an empty digit copies).
-__global__ void __launch_bounds__(BIG_THREADS)
-k_bin_order_big(const int32_t *__restrict__ cell_start, int32_t *unsorted, int32_t *perm,
-                const int32_t *__restrict__ big_list,
-                const int32_t *__restrict__ big_count, int32_t *big_next, int passes)
+// Step 3: each tile's row, the digit's first slot (the exclusive prefix of
+// the digit totals, formed by every block) plus the chunk's prefix plus the
+// counts of the chunk's earlier tiles.
+__global__ void __launch_bounds__(BIN_DIGITS)
+k_bin_scan_rows(const int32_t *__restrict__ hist, int nblk, const int32_t *__restrict__ csum,
+                const int32_t *__restrict__ total, int32_t *__restrict__ offs)
 {
-    __shared__ int32_t wcnt[BIG_WARPS][DIGITS];
-    __shared__ int32_t dtot[DIGITS];
-    __shared__ int32_t cur;
-    const int nbig = *big_count;
-    while (true) {
-        if (threadIdx.x == 0) cur = atomicAdd(big_next, 1);
-        __syncthreads();
-        const int k = cur;
-        __syncthreads();
-        if (k >= nbig) break;
-        const int c = big_list[k];
-        const int32_t b = cell_start[c];
-        const int n = cell_start[c + 1] - b;
-        for (int p = 0; p < passes; ++p) {
-            int32_t *src = (p & 1) ? perm + b : unsorted + b;
-            int32_t *dst = (p & 1) ? unsorted + b : perm + b;
-            block_digit_pass(src, dst, n, p * DIGIT_BITS, wcnt, dtot);
+    __shared__ int32_t wsum[BIN_DIGITS / 32];
+    const int c = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    const int v = total[d];
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= o) inc += n;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int before = lane < warp ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL_MASK, before, o);
+    int run = before + inc - v + csum[(int64_t)c * BIN_DIGITS + d];
+    const int t1 = min(nblk, (c + 1) * SCAN_TC);
+#pragma unroll 8
+    for (int t = c * SCAN_TC; t < t1; ++t) {
+        const int64_t i = (int64_t)t * BIN_DIGITS + d;
+        const int h = hist[i];
+        offs[i] = run;
+        run += h;
+    }
+}
+
+// cell_start[c] = the first sorted slot whose key is at least c (c = 0..nc;
+// cell_start[nc] = N): a binary search of the sorted keys per cell.
+__global__ void __launch_bounds__(256)
+k_bin_cell_start(const int32_t *__restrict__ keys, int64_t N, int64_t nc, int32_t *__restrict__ cell_start)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)keys[mid] < c)
+                lo = mid + 1;
+            else
+                hi = mid;
         }
+        cell_start[c] = (int32_t)lo;
     }
 }
 
@@ -650,41 +677,45 @@ k_radix_scatter(const int32_t *__restrict__ keys_in, const int32_t *__restrict__
 
 int radix_blocks(int64_t N) { return (int)((N + R_TILE - 1) / R_TILE); }
 
-// Binning workspace: the records in input order (16 B per particle), the
-// unsorted slot contents (4 B per particle), per-cell counts (then cursors)
-// and the big-cell list (4 B per cell each), two counters and the scan's
-// scratch.
+// Binning workspace: one set of pass buffers (key, index, record: 24 B per
+// particle), the other set's keys (its indices and records are perm and
+// sorted4 themselves: 4 B per particle), the per-tile digit counts and their
+// scan (4 B per digit and tile each: about 2 B per particle) and the scan's
+// chunk sums and digit totals.  Nothing scales with the number of cells.
 struct BinWs {
-    float4 *rec;
-    int32_t *unsorted;
-    int32_t *cnt;
-    int32_t *big_list;
-    int32_t *ctr;  // [0] big cells found, [1] big cells taken
-    char *scan_ws;
+    int32_t *keyX, *idxX;
+    float4 *recX;
+    int32_t *keyY;
+    int32_t *hist, *offs, *csum, *dtot;
     size_t total;
 };
+
+int bin_tiles(int64_t N) { return (int)((N + BIN_TILE - 1) / BIN_TILE); }
+int scan_chunks(int64_t N) { return (bin_tiles(N) + SCAN_TC - 1) / SCAN_TC; }
 
 BinWs bin_ws_layout(const hacc_mesh *mesh, void *ws)
 {
     BinWs b{};
     char *p = reinterpret_cast<char *>(ws);
     size_t off = 0;
-    const int64_t N = mesh->N, nc = mesh->n_cells;
+    const int64_t N = mesh->N;
+    const int64_t nhist = (int64_t)BIN_DIGITS * bin_tiles(N);
     auto take = [&](size_t bytes) {
         char *q = p ? p + off : nullptr;
         off += round_up(bytes, 256);
         return q;
     };
-    b.rec = reinterpret_cast<float4 *>(take((size_t)N * sizeof(float4)));
-    b.unsorted = reinterpret_cast<int32_t *>(take((size_t)N * 4));
-    b.cnt = reinterpret_cast<int32_t *>(take((size_t)nc * 4));
-    b.big_list = reinterpret_cast<int32_t *>(take((size_t)nc * 4));
-    b.ctr = reinterpret_cast<int32_t *>(take(2 * 4));
-    b.scan_ws = take(scan_workspace_bytes(nc));
+    b.recX = reinterpret_cast<float4 *>(take((size_t)N * sizeof(float4)));
+    b.keyX = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.idxX = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.keyY = reinterpret_cast<int32_t *>(take((size_t)N * 4));
+    b.hist = reinterpret_cast<int32_t *>(take((size_t)nhist * 4));
+    b.offs = reinterpret_cast<int32_t *>(take((size_t)nhist * 4));
+    b.csum = reinterpret_cast<int32_t *>(take((size_t)scan_chunks(N) * BIN_DIGITS * 4));
+    b.dtot = reinterpret_cast<int32_t *>(take((size_t)BIN_DIGITS * 4));
     b.total = off;
     return b;
 }
-
 }  // namespace
 
 size_t sort_workspace_bytes(int64_t N)
@@ -763,6 +794,7 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
     if ((dx || dy || dz) && !(dx && dy && dz)) return HACC_ERR_INVALID;
     if (!mesh || !out || !mesh->vols || mesh->V < 1 || mesh->N < 0 || mesh->n_cells < 1 || !status)
         return HACC_ERR_INVALID;
+    if (mesh->N >= ((int64_t)1 << 31) || mesh->n_cells >= ((int64_t)1 << 31)) return HACC_ERR_INVALID;
     if (!out->cell_start || !ws || !aligned16(ws)) return HACC_ERR_INVALID;
     const int64_t N = mesh->N, nc = mesh->n_cells;
     if (N > 0 && (!x || !y || !z || !m || !out->cell_of || !out->perm || !out->sorted4))
@@ -777,32 +809,60 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
         HACC_CUDA_TRY(cudaMemsetAsync(out->cell_start, 0, (size_t)(nc + 1) * 4, st));
         return HACC_OK;
     }
-    HACC_CUDA_TRY(cudaMemsetAsync(b.cnt, 0, (size_t)nc * 4, st));
-    HACC_CUDA_TRY(cudaMemsetAsync(b.ctr, 0, 2 * 4, st));
-    k_bin_keys<<<grid_for((N + PPL - 1) / PPL, KEY_THREADS), KEY_THREADS, 0, st>>>(mesh->vols, mesh->V, N, x, y, z, dx, dy, dz, m,
-                                                                 out->cell_of, b.rec, b.cnt, status,
-                                                                 out->mass_varies);
-    HACC_LAUNCH_CHECK();
-    int rc = scan_exclusive_i32(b.cnt, out->cell_start, nc, b.scan_ws, st);
-    if (rc) return rc;
-    // the counts are spent: their array becomes the per-cell cursor
-    HACC_CUDA_TRY(cudaMemcpyAsync(b.cnt, out->cell_start, (size_t)nc * 4, cudaMemcpyDeviceToDevice, st));
-    k_bin_slots<<<grid_for((N + PPL - 1) / PPL, KEY_THREADS), KEY_THREADS, 0, st>>>(N, out->cell_of, b.cnt, b.unsorted,
-                                                                                      status);
-    HACC_LAUNCH_CHECK();
-    float4 *s4 = reinterpret_cast<float4 *>(out->sorted4);
-    k_bin_order<<<grid_for((nc + 31) / 32 * 32, ORDER_THREADS), ORDER_THREADS, 0, st>>>(
-        nc, out->cell_start, b.unsorted, out->perm, b.big_list, b.ctr, N <= ((int64_t)1 << SEG_SHIFT));
-    HACC_LAUNCH_CHECK();
-    // index digits of the big cells' sort: enough for N - 1, an odd number of passes
+    const ParticleIn P{mesh->vols, mesh->V, x, y, z, dx, dy, dz, m};
+    const int nblk = bin_tiles(N);
+    // digits of the largest key, nc - 1: one pass per BIN_BITS of them
     int bits = 1;
-    while (bits < 31 && ((N - 1) >> bits) != 0) ++bits;
-    int passes = (bits + DIGIT_BITS - 1) / DIGIT_BITS;
-    if (passes % 2 == 0) ++passes;
-    k_bin_order_big<<<num_sms() * 4, BIG_THREADS, 0, st>>>(out->cell_start, b.unsorted, out->perm, b.big_list,
-                                                           b.ctr, b.ctr + 1, passes);
+    while (bits < 31 && ((nc - 1) >> bits) != 0) ++bits;
+    const int passes = (bits + BIN_BITS - 1) / BIN_BITS;
+    HACC_CUDA_TRY(cudaFuncSetAttribute(k_bin_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SCATTER_SMEM));
+    HACC_CUDA_TRY(cudaFuncSetAttribute(k_bin_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SCATTER_SMEM));
+    // persistent grids: blocks per SM of each kind
+    auto grid = [&](int per_sm) { return nblk < num_sms() * per_sm ? nblk : num_sms() * per_sm; };
+    float4 *s4 = reinterpret_cast<float4 *>(out->sorted4);
+    // the buffer sets alternate so that the last pass lands in perm and sorted4;
+    // pass 1's records go to the record buffer the first counting pass does not write
+    auto to_out = [&](int p) { return (passes - 1 - p) % 2 == 0; };
+    float4 *rec0 = to_out(0) ? b.recX : s4;
+    if (dx)
+        k_bin_keys<true><<<grid(2), BIN_THREADS, 0, st>>>(P, N, nblk, out->cell_of, rec0, b.hist, status,
+                                                          out->mass_varies);
+    else
+        k_bin_keys<false><<<grid(2), BIN_THREADS, 0, st>>>(P, N, nblk, out->cell_of, rec0, b.hist, status,
+                                                           out->mass_varies);
     HACC_LAUNCH_CHECK();
-    k_bin_gather<<<grid_for((N + PPL - 1) / PPL, KEY_THREADS), KEY_THREADS, 0, st>>>(N, out->perm, b.rec, s4);
+    const int32_t *kin = out->cell_of, *iin = nullptr;
+    const float4 *rin = rec0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * BIN_BITS;
+        if (p > 0) {
+            k_bin_hist<<<grid(3), BIN_THREADS, 0, st>>>(kin, N, shift, nblk, b.hist);
+            HACC_LAUNCH_CHECK();
+        }
+        const int nch = scan_chunks(N);
+        k_bin_scan_chunks<<<nch, BIN_DIGITS, 0, st>>>(b.hist, nblk, b.csum);
+        HACC_LAUNCH_CHECK();
+        k_bin_scan_digits<<<BIN_DIGITS / (BIN_DIGITS / 32), BIN_DIGITS, 0, st>>>(b.csum, nch, b.dtot);
+        HACC_LAUNCH_CHECK();
+        k_bin_scan_rows<<<nch, BIN_DIGITS, 0, st>>>(b.hist, nblk, b.csum, b.dtot, b.offs);
+        HACC_LAUNCH_CHECK();
+        int32_t *ko = to_out(p) ? b.keyY : b.keyX;
+        int32_t *io = to_out(p) ? out->perm : b.idxX;
+        float4 *ro = to_out(p) ? s4 : b.recX;
+        if (p == 0)
+            k_bin_scatter<true><<<grid(1), SC_THREADS, SCATTER_SMEM, st>>>(kin, nullptr, rin, (int)N, shift, nblk,
+                                                                            b.offs, ko, io, ro, status);
+        else
+            k_bin_scatter<false><<<grid(1), SC_THREADS, SCATTER_SMEM, st>>>(kin, iin, rin, (int)N, shift, nblk,
+                                                                             b.offs, ko, io, ro, status);
+        HACC_LAUNCH_CHECK();
+        kin = ko;
+        iin = io;
+        rin = ro;
+    }
+    k_bin_cell_start<<<grid_for(nc + 1, 256), 256, 0, st>>>(b.keyY, N, nc, out->cell_start);
     HACC_LAUNCH_CHECK();
     return HACC_OK;
 }

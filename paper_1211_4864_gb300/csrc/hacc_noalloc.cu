@@ -7,8 +7,8 @@
 
 namespace {
 
-// HACC_BIN_NOALLOC_BYTES (9 MiB): hacc_bin's scratch, about 20 bytes per
-// particle and 8 per cell (262,144 particles in up to 500,000 cells).
+// HACC_BIN_NOALLOC_BYTES (9 MiB): hacc_bin's scratch, about 30 bytes per
+// particle whatever the number of cells (262,144 particles fit).
 constexpr size_t NOALLOC_BIN_BYTES = HACC_BIN_NOALLOC_BYTES;
 
 // Loaded with the library onto every device that runs it, and held until the
@@ -57,8 +57,7 @@ extern "C" int hacc_bin_noalloc(const hacc_mesh *mesh, const float *x, const flo
     void *ws = nullptr;
     int rc = scratch_address(hacc::as_stream(stream), &ws);
     if (rc) return rc;
-    // hacc_bin clears the cell counts it accumulates and overwrites every
-    // other scratch word before reading it, so the previous call's contents
-    // never leak into this one.
+    // hacc_bin writes every scratch word before reading it, so the previous
+    // call's contents never leak into this one.
     return hacc_bin(mesh, x, y, z, nullptr, nullptr, nullptr, m, out, ws, NOALLOC_BIN_BYTES, status, stream);
 }

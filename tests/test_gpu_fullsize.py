@@ -215,10 +215,9 @@ def test_clustered256_rcb_tree_bit_exact_and_forces(clustered):
 
 
 def test_binning_bit_exact_beyond_2_26_particles():
-    """More than 2^26 particles: the binning's small-cell windows can no longer
-    pack (window cell, index) into one 32-bit key and sort one cell at a time
-    on the plain index; still bit-exact against the oracle (uniform particles,
-    about one per grid cell cubed)."""
+    """More than 2^26 particles (16,385 tiles per counting pass, indices of 27
+    bits, 16 million digit counts in each scan): bit-exact against the oracle
+    (uniform particles, about one per grid cell cubed)."""
     torch = need_cuda()
     import paper_1211_4864_gb300 as hs
     hs.load()

@@ -127,11 +127,10 @@ def test_bin_lists_tasks_bit_exact_uniform(torch, hs):
 
 @pytest.mark.parametrize("N", [200, 3000, 40000, 70000])
 def test_bin_bit_exact_when_one_cell_holds_most_particles(torch, hs, N):
-    """Degenerate clustering: most particles in one cell, the rest uniform.
-    The crowded cell takes each sorting path of the binning: 200 the warp's
-    shared-memory network, the others the block radix passes (index digits:
-    two significant bytes plus a copy pass at 3000 and 40000, three at
-    70000)."""
+    """Degenerate clustering: most particles in one cell, the rest uniform,
+    over one to 18 tiles of the binning's counting passes: nearly every item
+    of a tile shares one digit, so the ranks among equal digits span whole
+    warps and tiles."""
     rng = np.random.default_rng(N)
     L = np.float32(27.0)
     k = N * 9 // 10
@@ -144,11 +143,11 @@ def test_bin_bit_exact_when_one_cell_holds_most_particles(torch, hs, N):
     assert int(np.diff(sr.cell_start.cpu().numpy()).max()) >= k
 
 
-def test_bin_bit_exact_at_every_sorting_path_boundary(torch, hs):
-    """Cell sizes on both sides of every boundary between the binning's
-    sorting paths (windows of small cells filling exactly 32 lanes or one
-    more, the warp's shared-memory network up to 256, the block radix passes
-    above), in a shuffled input order; bit-exact against the oracle."""
+def test_bin_bit_exact_for_cells_of_every_size_class(torch, hs):
+    """Empty cells and cells of 1 to 1025 particles (sizes on both sides of
+    the powers of two up to a warp's 32 lanes and beyond, so that runs of one
+    digit start and end anywhere in a warp's items), in a shuffled input
+    order; bit-exact against the oracle."""
     sizes = [0, 1, 2, 15, 16, 17, 31, 32, 33, 0, 63, 64, 65, 127, 128, 129, 255, 256, 257, 0, 511, 512, 513, 1,
              1023, 1024, 1025]
     rng = np.random.default_rng(77)
@@ -164,6 +163,71 @@ def test_bin_bit_exact_at_every_sorting_path_boundary(torch, hs):
                  np.array([L], np.float32), np.array([0, N], np.int64))
     sr = check_bin_lists(torch, hs, w, 3.0, 3.0, split_T=128)
     assert sorted(np.diff(sr.cell_start.cpu().numpy()).tolist()) == sorted(sizes)
+
+
+def check_bin(torch, hs, w: Workload, cell_min, rcut, disp=None):
+    """Binning alone (no lists), bit-exact against the oracle per volume."""
+    sr = hs.ShortRange(w.L, w.vol_off, rcut, cell_min=cell_min)
+    pos, m = to_dev(torch, w)
+    d = None if disp is None else torch.tensor(disp, device="cuda")
+    sr.bin(pos[0], pos[1], pos[2], m, None if d is None else (d[0], d[1], d[2]))
+    torch.cuda.synchronize()
+    sr.check_status()
+    cell_of, cs = sr.cell_of.cpu().numpy(), sr.cell_start.cpu().numpy()
+    perm, s4 = sr.perm.cpu().numpy(), sr.sorted4.cpu().numpy()
+    cbase = 0
+    for v in range(w.V):
+        b, e = int(w.vol_off[v]), int(w.vol_off[v + 1])
+        ob = oracle.bin_volume(w.x[b:e], w.y[b:e], w.z[b:e], w.m[b:e], float(w.L[v]), cell_min,
+                               disp=None if disp is None else disp[:, b:e])
+        nc = ob["n"] ** 3
+        assert np.array_equal(cell_of[b:e], ob["cell_of"] + cbase)
+        assert np.array_equal(cs[cbase:cbase + nc + 1], ob["cell_start"] + b)
+        assert np.array_equal(perm[b:e], ob["perm"] + b)
+        assert np.array_equal(s4[b:e].view(np.int32), ob["sorted4"].view(np.int32))
+        cbase += nc
+    assert cbase == sr.n_cells
+    return sr
+
+
+def _half_clustered(N, L, seed):
+    """N particles in a box of side L: half uniform, half in eight tight
+    clumps (runs of equal cells in the input order), positions slightly
+    outside the box included."""
+    rng = np.random.default_rng(seed)
+    k = N // 2
+    centres = rng.random((8, 3)) * L
+    clump = centres[rng.integers(0, 8, N - k)] + rng.normal(size=(N - k, 3)) * 0.7
+    p = np.concatenate([rng.random((k, 3)) * L, clump]).astype(np.float32)
+    return Workload("half_clustered", p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(),
+                    rng.uniform(0.5, 2.0, N).astype(np.float32), np.zeros(N, np.float32),
+                    np.zeros(N, np.float32), np.zeros(N, np.float32), np.array([L], np.float32),
+                    np.array([0, N], np.int64))
+
+
+# (N, L, cell_min, rcut): one counting pass (at most 1024 cells: keys of ten bits), two
+# (2197 and 9261 cells) and three (102^3 = 1,061,208 cells: keys of 21 bits); N on both
+# sides of the 4096-particle tile of the passes, and several tiles with a ragged tail
+BIN_PASS_CASES = [(1, 27.0, 3.0, 3.0), (4095, 27.0, 3.0, 3.0), (4097, 27.0, 3.0, 3.0),
+                  (4096, 40.0, 3.0, 3.0), (3 * 4096 + 17, 40.0, 3.0, 3.0), (20000, 64.0, 3.0, 3.0),
+                  (3 * 4096 + 5, 102.0, 1.0, 1.0)]
+
+
+@pytest.mark.parametrize("N,L,cell_min,rcut", BIN_PASS_CASES)
+def test_bin_bit_exact_across_tiles_and_pass_counts(torch, hs, N, L, cell_min, rcut):
+    check_bin(torch, hs, _half_clustered(N, np.float32(L), seed=N), cell_min, rcut)
+
+
+def test_bin_with_displacements_bit_exact(torch, hs):
+    """Positions given as a reference plus a float32 displacement: the
+    position formed, wrapped and offset in float64 (two counting passes,
+    several tiles), bit-exact against the oracle."""
+    N, L = 3 * 4096 + 300, np.float32(40.0)
+    w = _half_clustered(N, L, seed=91)
+    rng = np.random.default_rng(91)
+    disp = (rng.normal(size=(3, N)) * 2.0).astype(np.float32)
+    disp[0, :4] = [0.5 * L, -0.5 * L, 1e-7, -1e-7]
+    check_bin(torch, hs, w, 3.0, 3.0, disp=disp)
 
 
 def test_bin_lists_bit_exact_fine_mesh_and_edge_positions(torch, hs):

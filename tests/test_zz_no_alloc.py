@@ -67,8 +67,9 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
 
 def test_noalloc_capacity_matches_the_documented_limit():
     """The scratch array holds hacc_bin's workspace for 262,144 particles in
-    500,000 cells; one that needs more is refused with a capacity error on the
-    host, before any device work."""
+    any number of cells (the workspace does not grow with the cells) but not
+    for 400,000; a problem that needs more is refused with a capacity error on
+    the host, before any device work."""
     from paper_1211_4864_gb300 import _lib
     from paper_1211_4864_gb300._lib import hacc_binned, hacc_mesh
     lib = _lib.load()
@@ -76,9 +77,10 @@ def test_noalloc_capacity_matches_the_documented_limit():
     mesh = hacc_mesh()
     mesh.V = 1
     mesh.N = 262144
-    mesh.n_cells = 500000
-    assert lib.hacc_bin_workspace_size(ctypes.byref(mesh)) <= limit
-    mesh.n_cells = 600000
+    for nc in (1, 500000, (1 << 31) - 1):
+        mesh.n_cells = nc
+        assert lib.hacc_bin_workspace_size(ctypes.byref(mesh)) <= limit
+    mesh.N = 400000
     assert lib.hacc_bin_workspace_size(ctypes.byref(mesh)) > limit
     out = hacc_binned()
     rc = lib.hacc_bin_noalloc(ctypes.byref(mesh), None, None, None, None, ctypes.byref(out), None, None)

@@ -541,9 +541,9 @@ def binning_rate(torch, sr, pos, m, w, peaks, reps=5):
             "frac": algo / (t_bin * 1e-3) / 1e9 / hbm,
             "cell_ordered_input": {"bin_ms": t_bin_c, "achieved_GBs": algo / (t_bin_c * 1e-3) / 1e9,
                                    "frac": algo / (t_bin_c * 1e-3) / 1e9 / hbm},
-            "note": "counting sort by cell: keys and counts, scan, atomic slots, per-cell index sort, record "
-                    "gather (random 16-byte reads); the slots and the sort's passes are not counted as "
-                    "algorithmic bytes"}
+            "note": "LSD counting sort by cell key carrying the records: keys, records and digit counts, "
+                    "two stable 10-bit digit passes, cell starts by binary search; the passes' "
+                    "intermediate reads and writes are not counted as algorithmic bytes"}
 
 
 def newton3(torch, sr, prm, launch, launch_sym, a, pairs, kernel, t_force, peak, fpp_g, fpp_s, reps=3):

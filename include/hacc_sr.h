@@ -432,8 +432,9 @@ size_t hacc_moments_workspace_size(int64_t N);
  *   out[0..2] = sum m v,  out[3..5] = sum m a  (zero by Newton's third law),
  *   out[6] = sum m |v|^2 / 2,  out[7] = sum m |a|,
  *   out[8] = sum m phi / 2 (the short-range potential energy; each pair once).
- * Each particle's terms and each thread's partial sums (a fixed stride of
- * particles) are formed in double-float arithmetic on the float32 pipe
+ * Each particle's terms and each thread's partial sums (groups of four
+ * consecutive particles at a fixed stride) are formed in double-float
+ * arithmetic on the float32 pipe
  * (exact products by fma, TwoSum accumulation, about 48 significant bits;
  * |a| by a float32 root plus one Newton correction), and the per-thread sums
  * are reduced in float64.  v (vx, vy, vz), a (ax, ay, az) and phi may each be

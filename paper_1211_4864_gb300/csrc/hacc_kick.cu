@@ -138,9 +138,61 @@ __device__ __forceinline__ void df_sqrt(float h, float l, float &rh, float &rl)
     rl = res / __fmul_rn(2.0f, r);
 }
 
+// Four consecutive values p[i..i+3] (i a multiple of 4): one 16-byte load when
+// p is 16-byte aligned, four 4-byte loads otherwise.
+__device__ __forceinline__ float4 load4(const float *__restrict__ p, int64_t i, bool aligned)
+{
+    if (aligned) return *reinterpret_cast<const float4 *>(p + i);
+    return make_float4(p[i], p[i + 1], p[i + 2], p[i + 3]);
+}
+
+__device__ __forceinline__ float lane4(const float4 &v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// One particle's terms added to the thread's double-float sums.
+__device__ __forceinline__ void moment_terms(DF (&s)[MOM_N], float mi, bool has_v, float v0, float v1, float v2,
+                                             bool has_a, float a0, float a1, float a2, bool has_phi, float ph)
+{
+    float p, e, h, l;
+    if (has_v) {
+        two_prod(mi, v0, p, e);
+        s[0].add(p, e);
+        two_prod(mi, v1, p, e);
+        s[1].add(p, e);
+        two_prod(mi, v2, p, e);
+        s[2].add(p, e);
+        df_norm2(v0, v1, v2, h, l);
+        df_mul(h, l, mi, p, e);
+        s[6].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));  // halving is exact
+    }
+    if (has_a) {
+        two_prod(mi, a0, p, e);
+        s[3].add(p, e);
+        two_prod(mi, a1, p, e);
+        s[4].add(p, e);
+        two_prod(mi, a2, p, e);
+        s[5].add(p, e);
+        float rh, rl;
+        df_norm2(a0, a1, a2, h, l);
+        df_sqrt(h, l, rh, rl);
+        df_mul(rh, rl, mi, p, e);
+        s[7].add(p, e);
+    }
+    if (has_phi) {
+        two_prod(mi, ph, p, e);
+        s[8].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));
+    }
+}
+
 // Fixed grid and fixed per-thread striding: the summation order depends only
-// on N, so the float64 results are reproducible run to run.  Per particle and
-// per thread in double-float (above), across threads and blocks in float64.
+// on N, so the float64 results are reproducible run to run.  Thread t takes
+// the groups of four consecutive particles t, t + T, t + 2T, ... (T threads;
+// each group's values by 16-byte loads where an array is aligned, all of a
+// group's loads issued before its arithmetic) and then particle
+// 4 floor(N / 4) + t of the last, partial group.  Per particle and per thread
+// in double-float (above), across threads and blocks in float64.
 __global__ void __launch_bounds__(MOM_THREADS)
 k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restrict__ vx, const float *__restrict__ vy,
                   const float *__restrict__ vz, const float *__restrict__ ax, const float *__restrict__ ay,
@@ -148,41 +200,37 @@ k_moments_partial(int64_t N, const float *__restrict__ m, const float *__restric
 {
     __shared__ double sh[MOM_THREADS / 32];
     DF s[MOM_N];
-#pragma unroll 4
-    for (int64_t i = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x; i < N; i += (int64_t)MOM_BLOCKS * MOM_THREADS) {
-        const float mi = m[i];
-        float p, e, h, l;
-        if (vx) {
-            const float v0 = vx[i], v1 = vy[i], v2 = vz[i];
-            two_prod(mi, v0, p, e);
-            s[0].add(p, e);
-            two_prod(mi, v1, p, e);
-            s[1].add(p, e);
-            two_prod(mi, v2, p, e);
-            s[2].add(p, e);
-            df_norm2(v0, v1, v2, h, l);
-            df_mul(h, l, mi, p, e);
-            s[6].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));  // halving is exact
+    const bool hv = vx != nullptr, ha = ax != nullptr, hp = phi != nullptr;
+    auto al = [](const float *p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const bool am = al(m), avx = al(vx), avy = al(vy), avz = al(vz), aax = al(ax), aay = al(ay), aaz = al(az),
+               aph = al(phi);
+    const int64_t t0 = (int64_t)blockIdx.x * MOM_THREADS + threadIdx.x;
+    const int64_t groups = N / 4;
+    for (int64_t g = t0; g < groups; g += (int64_t)MOM_BLOCKS * MOM_THREADS) {
+        const int64_t i = 4 * g;
+        const float4 m4 = load4(m, i, am);
+        float4 v0, v1, v2, a0, a1, a2, p4;
+        if (hv) {
+            v0 = load4(vx, i, avx);
+            v1 = load4(vy, i, avy);
+            v2 = load4(vz, i, avz);
         }
-        if (ax) {
-            const float a0 = ax[i], a1 = ay[i], a2 = az[i];
-            two_prod(mi, a0, p, e);
-            s[3].add(p, e);
-            two_prod(mi, a1, p, e);
-            s[4].add(p, e);
-            two_prod(mi, a2, p, e);
-            s[5].add(p, e);
-            float rh, rl;
-            df_norm2(a0, a1, a2, h, l);
-            df_sqrt(h, l, rh, rl);
-            df_mul(rh, rl, mi, p, e);
-            s[7].add(p, e);
+        if (ha) {
+            a0 = load4(ax, i, aax);
+            a1 = load4(ay, i, aay);
+            a2 = load4(az, i, aaz);
         }
-        if (phi) {
-            two_prod(mi, phi[i], p, e);
-            s[8].add(__fmul_rn(0.5f, p), __fmul_rn(0.5f, e));
-        }
+        if (hp) p4 = load4(phi, i, aph);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            moment_terms(s, lane4(m4, k), hv, hv ? lane4(v0, k) : 0.f, hv ? lane4(v1, k) : 0.f,
+                         hv ? lane4(v2, k) : 0.f, ha, ha ? lane4(a0, k) : 0.f, ha ? lane4(a1, k) : 0.f,
+                         ha ? lane4(a2, k) : 0.f, hp, hp ? lane4(p4, k) : 0.f);
     }
+    const int64_t i = 4 * groups + t0;
+    if (i < N)
+        moment_terms(s, m[i], hv, hv ? vx[i] : 0.f, hv ? vy[i] : 0.f, hv ? vz[i] : 0.f, ha, ha ? ax[i] : 0.f,
+                     ha ? ay[i] : 0.f, ha ? az[i] : 0.f, hp, hp ? phi[i] : 0.f);
 #pragma unroll
     for (int k = 0; k < MOM_N; ++k) {
         double r = block_sum(s[k].value(), sh);

@@ -111,8 +111,8 @@ constexpr size_t SM_INV = SM_CNT + sizeof(uint32_t) * SC_WARPS * SC_WORDS;
 constexpr size_t SM_TSTART = SM_INV + sizeof(uint16_t) * BIN_TILE;
 constexpr size_t SM_WSUM = SM_TSTART + sizeof(int32_t) * BIN_DIGITS;
 constexpr size_t SCATTER_SMEM = SM_WSUM + sizeof(int32_t) * SC_WARPS;
-static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS == SC_THREADS && SC_WARPS % 2 == 0,
-              "one digit per thread in the scan, two digit words per thread in the prefix");
+static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS == SC_THREADS,
+              "one digit's first global slot per thread");
 static_assert(SCATTER_SMEM <= 227 * 1024, "shared memory of one block");
 static_assert(BIN_TILE <= 65536, "16-bit tile positions");
 
@@ -376,49 +376,37 @@ k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ id
             slot[k] = (int)((old >> half) & 0xffffu) + __popc(peers & lt);
         }
         __syncthreads();
-        // per digit pair: exclusive prefix over the warps (both halves at
-        // once: a tile's count per digit stays below 2^16), and the tile's
-        // count per digit
-        // (thread j + 512 h takes warps [16 h, 16 h + 16) of word j; the
-        // upper half then adds the lower half's total)
-        {
-            constexpr int HW = SC_WARPS / 2;
-            const int j = threadIdx.x & (BIN_DIGITS / 2 - 1), h = threadIdx.x / (BIN_DIGITS / 2);
+        // per digit pair j (thread j < 512): exclusive prefix over the warps
+        // of the packed counts (both halves at once: a tile's count per digit
+        // stays below 2^16), then the tile's exclusive scan of the digit
+        // counts, two digits per thread: its first local slot per digit
+        if (threadIdx.x < BIN_DIGITS / 2) {
+            const int j = threadIdx.x;
             uint32_t run = 0u;
 #pragma unroll
-            for (int w = h * HW; w < (h + 1) * HW; ++w) {
+            for (int w = 0; w < SC_WARPS; ++w) {
                 const uint32_t c = wcnt[w][j];
                 wcnt[w][j] = run;
                 run += c;
             }
-            if (h == 0) tstart[2 * j] = (int)run;  // the lower half's packed total, for the upper half
-            __syncthreads();
-            if (h == 1) {
-                const uint32_t lower = (uint32_t)tstart[2 * j];
-#pragma unroll
-                for (int w = HW; w < SC_WARPS; ++w) wcnt[w][j] += lower;
-                run += lower;
-                tstart[2 * j] = (int)(run & 0xffffu);
-                tstart[2 * j + 1] = (int)(run >> 16);
-            }
-        }
-        __syncthreads();
-        // exclusive scan of the tile's digit counts (one per thread): its
-        // first local slot per digit
-        {
-            const int v = tstart[threadIdx.x];
-            int inc = v;
+            const int c0 = (int)(run & 0xffffu), c1 = (int)(run >> 16);
+            int inc = c0 + c1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int n = __shfl_up_sync(FULL_MASK, inc, o);
                 if (lane >= o) inc += n;
             }
             if (lane == 31) wsum[warp] = inc;
-            __syncthreads();
+            tstart[2 * j] = inc - c0 - c1;  // within the warp, completed below
+            tstart[2 * j + 1] = inc - c1;
+        }
+        __syncthreads();
+        if (threadIdx.x < BIN_DIGITS / 2) {
             int before = lane < warp ? wsum[lane] : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(FULL_MASK, before, o);
-            tstart[threadIdx.x] = before + inc - v;
+            tstart[2 * threadIdx.x] += before;
+            tstart[2 * threadIdx.x + 1] += before;
         }
         __syncthreads();
 #pragma unroll

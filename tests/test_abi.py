@@ -133,3 +133,14 @@ def test_device_calls_reject_bad_arguments_on_host(lib):
                          None) == _lib.HACC_ERR_INVALID
     assert lib.hacc_moments(5, None, None, None, None, None, None, None, None, None, None, 0,
                             None) == _lib.HACC_ERR_INVALID
+    # 32-bit slots and keys: N and n_cells below 2^31 (checked before any device work; the
+    # pointers are never dereferenced)
+    for n, nc in (((1 << 31), 27), (1000, (1 << 31))):
+        big = _lib.hacc_mesh()
+        big.vols = 16
+        big.V = 1
+        big.N = n
+        big.n_cells = nc
+        out = _lib.hacc_binned()
+        assert lib.hacc_bin(ctypes.byref(big), None, None, None, None, None, None, None, ctypes.byref(out), None,
+                            0, ctypes.c_void_p(16), None) == _lib.HACC_ERR_INVALID

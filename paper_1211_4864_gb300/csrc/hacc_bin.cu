@@ -7,19 +7,18 @@
 // particle's record through its passes, so that every pass reads its input
 // in order and writes its output in runs of consecutive slots (no atomics
 // on global memory, no random gathers):
-//   1. k_bin_keys: per particle its cell key (cell_of, input order) and, per
-//      tile of BIN_TILE particles, the counts of the key's lowest 10-bit
-//      digit;
-//   2. an exclusive scan of those counts, digit-major: each tile's first
-//      slot for each digit;
-//   3. k_bin_scatter, once per digit from the lowest: each tile's particles
-//      ranked stably by the digit (warp match masks and per-warp counters, so
-//      equal digits keep the tile's order), staged in shared memory in digit
-//      order and stored to their slots -- key, input index and the
-//      (offset, mass) record (the first pass forms the record from the
-//      positions; later passes move it).  Before each later pass k_bin_hist
-//      counts the next digit per tile of the previous pass's output.  The
-//      last pass writes perm and sorted4 themselves;
+//   1. k_bin_keys: per particle its cell key (cell_of) and its (offset, mass)
+//      record, both in input order, and per tile of BIN_TILE particles the
+//      counts of the key's lowest 10-bit digit, a row per tile;
+//   2. a column scan of those rows (k_bin_scan_chunks, _digits, _rows): each
+//      tile's first slot for each digit;
+//   3. k_bin_scatter, once per digit from the lowest: each tile's key, index
+//      and record copied into shared memory, its keys ranked stably by the
+//      digit (warp match masks and per-warp counters, so equal digits keep
+//      the tile's order), and the tile stored to its slots in digit order.
+//      Before each later pass k_bin_hist counts the next digit per tile of
+//      the previous pass's output.  The last pass writes perm and sorted4
+//      themselves;
 //   4. k_bin_cell_start: each cell's first slot by binary search of the
 //      sorted keys.
 // Each pass is stable, so within a cell the order is ascending input index.
@@ -187,10 +186,11 @@ __device__ __forceinline__ void count_digit(int32_t *cnt, int d)
 
 // Pass 1: per particle its cell key (cell_of) and its (offset, mass) record
 // (rec), both in input order; per tile (particles [t BIN_TILE, (t + 1)
-// BIN_TILE)) the counts of the key's lowest digit, digit-major into hist
-// (hist[t BIN_DIGITS + d], a row per tile); with mass_varies, whether any mass differs from the
-// first particle's (N > 0).  Persistent blocks take tiles in turn and ask
-// the L2 for their next tile's inputs while they work on the current one.
+// BIN_TILE)) the counts of the key's lowest digit into hist (a row per
+// tile, hist[t BIN_DIGITS + d]); with mass_varies, whether any mass differs
+// from the first particle's (N > 0).  Persistent blocks take tiles in turn
+// and ask the L2 for their next tile's inputs while they work on the
+// current one.
 // DISP: displacements are given (the float64 position path).
 template <bool DISP>
 __global__ void __launch_bounds__(BIN_THREADS, 2)

@@ -91,28 +91,26 @@ constexpr int BIN_THREADS = 512;
 constexpr int BIN_ITEMS = 8;
 constexpr int BIN_TILE = BIN_THREADS * BIN_ITEMS;  // 4096 particles per tile
 
-// k_bin_scatter: one block of SC_THREADS per SM, SC_ITEMS items per thread.
-constexpr int SC_THREADS = 1024;
+// k_bin_scatter: two blocks of SC_THREADS per SM, SC_ITEMS items per thread.
+constexpr int SC_THREADS = 512;
 constexpr int SC_WARPS = SC_THREADS / 32;
 constexpr int SC_ITEMS = BIN_TILE / SC_THREADS;
 constexpr int SC_WORDS = BIN_DIGITS / 2 + 1;  // per-warp counters, two 16-bit digits a word; the
                                               // last word takes the items past N
-// Its shared memory: the tile's inputs (copied in asynchronously; keys and
-// the tile's first global slot per digit double-buffered, one tile ahead),
-// the per-warp counters, the inverse of the tile's digit order, the tile's
-// first local slot per digit and the warp totals of the scan.
-constexpr size_t SM_REC = 0;
-constexpr size_t SM_IDX = SM_REC + sizeof(float4) * BIN_TILE;
-constexpr size_t SM_KEY = SM_IDX + sizeof(int32_t) * BIN_TILE;               // [2][BIN_TILE]
+// Its shared memory: the tile's keys and its first global slot per digit
+// (copied in asynchronously, double-buffered, one tile ahead), the per-warp
+// counters, the inverse of the tile's digit order, the tile's first local
+// slot per digit and the warp totals of the scan.
+constexpr size_t SM_KEY = 0;                                                  // [2][BIN_TILE]
 constexpr size_t SM_BASE = SM_KEY + 2 * sizeof(int32_t) * BIN_TILE;          // [2][BIN_DIGITS]
 constexpr size_t SM_CNT = SM_BASE + 2 * sizeof(int32_t) * BIN_DIGITS;
 constexpr size_t SM_INV = SM_CNT + sizeof(uint32_t) * SC_WARPS * SC_WORDS;
 constexpr size_t SM_TSTART = SM_INV + sizeof(uint16_t) * BIN_TILE;
 constexpr size_t SM_WSUM = SM_TSTART + sizeof(int32_t) * BIN_DIGITS;
 constexpr size_t SCATTER_SMEM = SM_WSUM + sizeof(int32_t) * SC_WARPS;
-static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS == SC_THREADS,
-              "one digit's first global slot per thread");
-static_assert(SCATTER_SMEM <= 227 * 1024, "shared memory of one block");
+static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS / 2 == SC_THREADS,
+              "one digit pair per thread in the prefix");
+static_assert(2 * SCATTER_SMEM <= 227 * 1024, "shared memory of two blocks");
 static_assert(BIN_TILE <= 65536, "16-bit tile positions");
 
 // Asynchronous copies of 4 and 16 bytes from global to shared memory
@@ -300,15 +298,13 @@ k_bin_hist(const int32_t *__restrict__ keys, int64_t N, int shift, int nblk, int
 // position), otherwise the previous pass's (key, index, record) arrays.
 // N < 2^31.
 template <bool FIRST>
-__global__ void __launch_bounds__(SC_THREADS, 1)
+__global__ void __launch_bounds__(SC_THREADS, 2)
 k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ idx_in,
               const float4 *__restrict__ rec_in, int N, int shift, int nblk, const int32_t *__restrict__ offs,
               int32_t *__restrict__ key_out, int32_t *__restrict__ idx_out, float4 *__restrict__ rec_out,
               uint32_t *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *srec = reinterpret_cast<float4 *>(smem + SM_REC);
-    int32_t *sidx = reinterpret_cast<int32_t *>(smem + SM_IDX);
     int32_t *skey2 = reinterpret_cast<int32_t *>(smem + SM_KEY);
     int32_t *base2 = reinterpret_cast<int32_t *>(smem + SM_BASE);
     uint32_t(*wcnt)[SC_WORDS] = reinterpret_cast<uint32_t(*)[SC_WORDS]>(smem + SM_CNT);
@@ -326,7 +322,8 @@ k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ id
             for (int k = 0; k < SC_ITEMS; ++k)
                 if (tile0 + l0 + 32 * k < N)
                     async_copy4(skey2 + b * BIN_TILE + l0 + 32 * k, key_in + tile0 + l0 + 32 * k);
-            async_copy4(base2 + b * BIN_DIGITS + threadIdx.x, offs + (int64_t)t * BIN_DIGITS + threadIdx.x);
+            for (int d = threadIdx.x; d < BIN_DIGITS; d += SC_THREADS)
+                async_copy4(base2 + b * BIN_DIGITS + d, offs + (int64_t)t * BIN_DIGITS + d);
         }
         async_commit();
     };
@@ -339,23 +336,13 @@ k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ id
         async_wait<0>();  // this tile's keys and slots (fetched during the previous tile)
         for (int i = threadIdx.x; i < SC_WARPS * SC_WORDS; i += SC_THREADS) (&wcnt[0][0])[i] = 0u;
         __syncthreads();
-        // the tile's indices and records land while its keys are ranked; the
-        // next tile's keys and slots while this one is stored
-#pragma unroll
-        for (int k = 0; k < SC_ITEMS; ++k) {
-            const int l = l0 + 32 * k;
-            if (tile0 + l < N) {
-                if (!FIRST) async_copy4(sidx + l, idx_in + tile0 + l);
-                async_copy16(srec + l, rec_in + tile0 + l);
-            }
-        }
-        async_commit();
+        // the L2 fetches this tile's indices and records while its keys are
+        // ranked; the next tile's keys and slots land while this one is stored
         fetch_keys(t + gridDim.x, buf ^ 1);
         if (threadIdx.x == 0) {
-            const int tn = t + 2 * gridDim.x;
-            prefetch_tile(key_in, tn, N);
-            prefetch_tile(rec_in, t + gridDim.x, N);
-            if (!FIRST) prefetch_tile(idx_in, t + gridDim.x, N);
+            prefetch_tile(rec_in, t, N);
+            if (!FIRST) prefetch_tile(idx_in, t, N);
+            prefetch_tile(key_in, t + 2 * gridDim.x, N);
         }
         int32_t key[SC_ITEMS];
         int slot[SC_ITEMS];
@@ -417,23 +404,41 @@ k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ id
                     (uint16_t)(l0 + 32 * k);
             }
         }
-        async_wait<1>();  // this tile's indices and records (the next tile's keys may still be in flight)
         __syncthreads();
+        // the tile in digit order: each item's index and record gathered from
+        // the tile's range of the input (in L2), G items' loads in flight together
         const int nv = N - tile0 < BIN_TILE ? N - tile0 : BIN_TILE;
-        for (int j = threadIdx.x; j < nv; j += SC_THREADS) {
-            const int l = inv[j];
-            const int32_t kk = skey[l];
-            const int d = key_digit(kk, shift);
-            const int pos = base_d[d] + (j - tstart[d]);
-#ifdef HACC_DEBUG_BOUNDS
-            if (pos < 0 || pos >= N) {
-                atomicOr(status, HACC_STATUS_BOUNDS);
-                continue;
+        constexpr int G = 4;
+        for (int j0 = threadIdx.x; j0 < nv; j0 += G * SC_THREADS) {
+            int l[G];
+            int32_t ix[G];
+            float4 r[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int j = j0 + g * SC_THREADS;
+                l[g] = j < nv ? inv[j] : 0;
+                if (j < nv) {
+                    ix[g] = FIRST ? tile0 + l[g] : idx_in[tile0 + l[g]];
+                    r[g] = rec_in[tile0 + l[g]];
+                }
             }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int j = j0 + g * SC_THREADS;
+                if (j >= nv) break;
+                const int32_t kk = skey[l[g]];
+                const int d = key_digit(kk, shift);
+                const int pos = base_d[d] + (j - tstart[d]);
+#ifdef HACC_DEBUG_BOUNDS
+                if (pos < 0 || pos >= N) {
+                    atomicOr(status, HACC_STATUS_BOUNDS);
+                    continue;
+                }
 #endif
-            key_out[pos] = kk;
-            idx_out[pos] = FIRST ? tile0 + l : sidx[l];
-            rec_out[pos] = srec[l];
+                key_out[pos] = kk;
+                idx_out[pos] = ix[g];
+                rec_out[pos] = r[g];
+            }
         }
         __syncthreads();  // shared memory is reused by the next tile
     }
@@ -840,10 +845,10 @@ extern "C" int hacc_bin(const hacc_mesh *mesh, const float *x, const float *y, c
         int32_t *io = to_out(p) ? out->perm : b.idxX;
         float4 *ro = to_out(p) ? s4 : b.recX;
         if (p == 0)
-            k_bin_scatter<true><<<grid(1), SC_THREADS, SCATTER_SMEM, st>>>(kin, nullptr, rin, (int)N, shift, nblk,
+            k_bin_scatter<true><<<grid(2), SC_THREADS, SCATTER_SMEM, st>>>(kin, nullptr, rin, (int)N, shift, nblk,
                                                                             b.offs, ko, io, ro, status);
         else
-            k_bin_scatter<false><<<grid(1), SC_THREADS, SCATTER_SMEM, st>>>(kin, iin, rin, (int)N, shift, nblk,
+            k_bin_scatter<false><<<grid(2), SC_THREADS, SCATTER_SMEM, st>>>(kin, iin, rin, (int)N, shift, nblk,
                                                                              b.offs, ko, io, ro, status);
         HACC_LAUNCH_CHECK();
         kin = ko;

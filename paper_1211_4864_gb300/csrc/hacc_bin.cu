@@ -113,17 +113,11 @@ static_assert(SC_ITEMS * SC_THREADS == BIN_TILE && BIN_DIGITS / 2 == SC_THREADS,
 static_assert(2 * SCATTER_SMEM <= 227 * 1024, "shared memory of two blocks");
 static_assert(BIN_TILE <= 65536, "16-bit tile positions");
 
-// Asynchronous copies of 4 and 16 bytes from global to shared memory
-// (cp.async), their commit and wait.
+// Asynchronous copy of 4 bytes from global to shared memory (cp.async), its
+// commit and wait.
 __device__ __forceinline__ void async_copy4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void async_copy16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -283,20 +277,20 @@ k_bin_hist(const int32_t *__restrict__ keys, int64_t N, int shift, int nblk, int
     }
 }
 
-// One stable counting pass by the digit at `shift`.  Persistent blocks, one
+// One stable counting pass by the digit at `shift`.  Persistent blocks, two
 // per SM, take tiles in turn.  In tile t, warp w owns tile positions
 // [w 32 SC_ITEMS, (w + 1) 32 SC_ITEMS) and item k of lane l is position
 // w 32 SC_ITEMS + 32 k + l, so (warp, item, lane) order is input order and
 // equal digits keep it: an item's slot is the tile's first slot for its
 // digit (offs, the scanned counts) plus the number of earlier items of the
-// tile with that digit (per-warp counters).  Each thread copies its items'
-// key, index and record into shared memory asynchronously; the keys are
-// ranked while the rest lands.  The tile's items are then stored in digit
-// order (through the inverse of the ranking), so the stores to global memory
-// run along each digit's consecutive slots.  FIRST: the input is pass 1's
-// output (keys cell_of, records in input order; an item's index is its
-// position), otherwise the previous pass's (key, index, record) arrays.
-// N < 2^31.
+// tile with that digit (per-warp counters).  The tile's keys and first
+// slots arrive in shared memory asynchronously, one tile ahead; while the
+// keys are ranked the L2 fetches the tile's indices and records, which the
+// store loop then gathers in digit order (through the inverse of the
+// ranking), so the stores to global memory run along each digit's
+// consecutive slots.  FIRST: the input is pass 1's output (keys cell_of,
+// records in input order; an item's index is its position), otherwise the
+// previous pass's (key, index, record) arrays.  N < 2^31.
 template <bool FIRST>
 __global__ void __launch_bounds__(SC_THREADS, 2)
 k_bin_scatter(const int32_t *__restrict__ key_in, const int32_t *__restrict__ idx_in,

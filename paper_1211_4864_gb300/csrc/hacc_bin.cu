@@ -12,10 +12,10 @@
 //      counts of the key's lowest 10-bit digit, a row per tile;
 //   2. a column scan of those rows (k_bin_scan_chunks, _digits, _rows): each
 //      tile's first slot for each digit;
-//   3. k_bin_scatter, once per digit from the lowest: each tile's key, index
-//      and record copied into shared memory, its keys ranked stably by the
-//      digit (warp match masks and per-warp counters, so equal digits keep
-//      the tile's order), and the tile stored to its slots in digit order.
+//   3. k_bin_scatter, once per digit from the lowest: each tile's keys
+//      ranked stably by the digit in shared memory (warp match masks and
+//      per-warp counters, so equal digits keep the tile's order), then its
+//      keys, indices and records stored to their slots in digit order.
 //      Before each later pass k_bin_hist counts the next digit per tile of
 //      the previous pass's output.  The last pass writes perm and sorted4
 //      themselves;

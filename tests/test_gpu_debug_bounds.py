@@ -95,6 +95,31 @@ def test_debug_build_matches_product_build_on_clean_input(torch, hs):
     assert rms < RMS_TOL
 
 
+def test_debug_build_binning_is_the_product_binning(torch, hs):
+    """The debug build also checks every slot the binning's counting passes
+    store to; on clean input it reports nothing and bins bit for bit as the
+    product build (clustered particles over several tiles, two passes)."""
+    from paper_1211_4864_gb300 import _lib
+    from synth.workloads import clustered_box
+    w = clustered_box(32, 20, seed=9)
+    sr = hs.ShortRange(w.L, w.vol_off, RC)
+    pos = torch.tensor(np.stack([w.x, w.y, w.z]), device="cuda")
+    m = torch.tensor(w.m, device="cuda")
+    outs = []
+    for debug in (False, True):
+        prev = _lib.use_library(debug=debug)
+        try:
+            sr.status.zero_()
+            sr.bin(pos[0], pos[1], pos[2], m)
+            torch.cuda.synchronize()
+            assert hs.hacc_get_status(sr.status) == 0
+            outs.append([t.cpu().numpy().copy() for t in (sr.cell_of, sr.cell_start, sr.perm, sr.sorted4)])
+        finally:
+            _lib._lib = prev
+    for g, r in zip(outs[1], outs[0]):
+        assert np.array_equal(g.view(np.int32), r.view(np.int32))
+
+
 @pytest.mark.parametrize("what", ["list entry", "list image code", "task slots", "task count"])
 def test_corrupted_lists_and_tasks_are_reported_not_read(torch, hs, debug_lib, what):
     w, c, prm, sr, pos, m, lam = _case(torch, hs, seed=22)

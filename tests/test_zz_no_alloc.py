@@ -50,6 +50,24 @@ def test_noalloc_binning_matches_workspace_binning_twice():
             assert np.array_equal(g.view(np.int32), r.view(np.int32))
 
 
+@pytest.mark.gpu
+def test_noalloc_binning_at_its_documented_limit():
+    """262,144 clustered particles (the documented capacity of the fixed
+    scratch array; two counting passes over 64 tiles): bit for bit what
+    hacc_bin gives with a workspace."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1211_4864_gb300 as hs
+    hs.load()
+    w = clustered_box(64, 100, seed=4)
+    assert w.N == 262144
+    got = _run(hs, torch, w, noalloc=True)
+    ref = _run(hs, torch, w, noalloc=False)
+    for g, r in zip(got, ref):
+        assert np.array_equal(g.view(np.int32), r.view(np.int32))
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     """Too large for the fixed array: a clear capacity error, checked on the
     host before any device work."""

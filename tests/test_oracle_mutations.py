@@ -40,6 +40,9 @@ MUTANTS = [
     ("unstable placement", "for (int64_t i = 0; i < N; ++i) {\n        int64_t k = cnt[cell_of[i]]++;",
      "for (int64_t i = N - 1; i >= 0; --i) {\n        int64_t k = cnt[cell_of[i]]++;"),
     ("wrap correction dropped", "    if (xw >= L) xw = xw - L;\n    return xw;", "    return xw;"),
+    ("cell key axes swapped", "int32_t c = (cz * n + cy) * n + cx;", "int32_t c = (cx * n + cy) * n + cz;"),
+    ("float64 wrap correction dropped", "    if (pw >= L) pw = pw - L;\n    return pw;", "    return pw;"),
+    ("displaced position rounded before the offset", "*o = (float)(pw - (double)ctr);", "*o = (float)pw - ctr;"),
     ("stencil row missing", "for (int dz = -R; dz <= R; ++dz)", "for (int dz = -R; dz < R; ++dz)"),
     ("image shift sign", "if (px < 0) { px += n; sx = -1; }", "if (px < 0) { px += n; sx = 1; }"),
     ("cell origin offset", "float ctr = ((float)c + 0.5f) * w;\n        *o = xw - ctr;",

@@ -404,6 +404,9 @@ def test_binning_with_displacements_keeps_float64_positions():
     z = (rng.random(N) * L).astype(np.float32)
     d = (rng.normal(size=(3, N)) * 1e-3).astype(np.float32)
     d[0, :3] = [-x[0] - np.float32(1e-6), np.float32(70.0), np.float32(-64.5)]
+    # y + d = -1e-20: p - floor(p / L) L rounds to L itself, which the wrap's
+    # correction step brings back to 0
+    y[3], d[1, 3] = np.float32(0.0), np.float32(-1e-20)
     m = np.ones(N, np.float32)
     b = oracle.bin_volume(x, y, z, m, float(L), 3.0, disp=d)
     n, w, iw = b["n"], b["w"], b["inv_w"]

@@ -290,9 +290,11 @@ class ShortRange:
         self.tasks = torch.empty((max(self.task_cap, 1), 4), dtype=i32, device=dev)
         self.task_order = torch.empty(max(self.task_cap, 1), dtype=i32, device=dev)
         self._alloc_entries(self.entry_cap)
-        ws_bytes = max(build_ws, lib.hacc_force_workspace_size(ctypes.byref(self.mesh)),
-                       lib.hacc_moments_workspace_size(N))
+        ws_bytes = max(build_ws, lib.hacc_force_workspace_size(ctypes.byref(self.mesh)))
         self.ws = torch.empty(int(ws_bytes), dtype=torch.uint8, device=dev)
+        # the moments keep their own (small) scratch, so that they may run on another stream
+        # while the next binning, lists or force call uses ws
+        self.mom_ws = torch.empty(int(lib.hacc_moments_workspace_size(N)), dtype=torch.uint8, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
 
     def _alloc_entries(self, cap: int):
@@ -400,7 +402,7 @@ class ShortRange:
             vx, vy, vz = v[0], v[1], v[2]
         if a is not None:
             ax, ay, az = a[0], a[1], a[2]
-        hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.ws, phi)
+        hacc_moments(self.N, m, vx, vy, vz, ax, ay, az, out, self.mom_ws, phi)
         return out
 
     def potential(self, params: SRParams, out=None, launch: Launch | None = None):
